@@ -1,0 +1,194 @@
+"""Pins of the oracle's full step against what the physics fixes.
+
+- conservation with the flux off (periodic): red mass, blue mass and momentum to round-off;
+- Eq. (exchange): with the flux on, total mass and momentum stay put and the red mass lost equals
+  the FP64 ledger sum of varphi = phi / S-bar over sites (Sec. II.B);
+- walls and solid obstacles conserve mass;
+- mirror symmetry of a centred drop (no noise);
+- the single-component limit is plain BGK: a shear wave decays as exp(-nu k^2 t),
+  nu = c_s^2 (tau - 1/2) (Sec. II.A);
+- a static drop obeys Laplace's law dp = sigma / R (2D), with p from Eq. (EOS);
+- the sampled step equals the full step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_14859_gb300 import inputs
+
+
+def totals(run):
+    m = run.macros()
+    rho = m["rho_r"] + m["rho_b"]
+    return m["rho_r"].sum(), m["rho_b"].sum(), (rho * m["u"]).reshape(3, -1).sum(axis=1)
+
+
+def drop_params(q, shape, **kw):
+    nz, ny, nx = shape
+    base = dict(q=q, nx=nx, ny=ny, nz=nz, sigma=inputs.sigma_from_amplitude(0.01), beta=0.7,
+                site_rule=oracle.RULE_BAND, threshold=0.5, sbar=3.0, phi=0.0)
+    base.update(kw)
+    return oracle.Params(**base)
+
+
+def make_run(p, R0, noise=1e-6, seed=5, center=None):
+    shape = p.shape
+    rn = inputs.sphere_phase(shape, center or inputs.centred(shape), R0)
+    nz = inputs.uniform_noise((2, p.q) + shape, noise, seed) if noise else None
+    return oracle.Run(p, oracle.init(p, rn, nz))
+
+
+@pytest.mark.parametrize("q,shape,steps,gamma", [(9, (1, 24, 32), 300, 1.0),
+                                                  (9, (1, 24, 32), 200, 4.0),
+                                                  (19, (10, 12, 14), 40, 1.0),
+                                                  (19, (10, 12, 14), 30, 10.0)])
+def test_conservation_flux_off(q, shape, steps, gamma):
+    p = drop_params(q, shape, rho_r_in=gamma, tau_b=0.8)
+    run = make_run(p, R0=min(shape[1:]) / 4)
+    r0, b0, j0 = totals(run)
+    run.step(steps)
+    r1, b1, j1 = totals(run)
+    assert abs(r1 - r0) <= 1e-13 * r0
+    assert abs(b1 - b0) <= 1e-13 * b0
+    assert np.all(np.abs(j1 - j0) <= 1e-13 * (r0 + b0))
+    assert run.evaporated == 0.0
+
+
+@pytest.mark.parametrize("rule,thr", [(oracle.RULE_BAND, 0.5), (oracle.RULE_GRADIENT, 0.05)])
+@pytest.mark.parametrize("q,shape", [(9, (1, 32, 32)), (19, (12, 12, 12))])
+def test_exchange_bookkeeping(q, shape, rule, thr):
+    p = drop_params(q, shape, site_rule=rule, threshold=thr, phi=3e-3, sbar=2.5)
+    run = make_run(p, R0=shape[1] / 4)
+    r0, b0, j0 = totals(run)
+    run.step(60)
+    r1, b1, j1 = totals(run)
+    assert run.ledger.site_steps > 0
+    assert abs((r1 + b1) - (r0 + b0)) <= 1e-13 * (r0 + b0)
+    assert abs((r0 - r1) - run.evaporated) <= 1e-12 * r0
+    assert np.all(np.abs(j1 - j0) <= 1e-13 * (r0 + b0))
+    # every site moves exactly phi / S-bar per step
+    assert run.ledger.last_removed == pytest.approx(run.ledger.last_sites * 3e-3 / 2.5, rel=1e-12)
+
+
+def test_flux_field_and_ledger():
+    shape = (1, 24, 24)
+    phi = inputs.uniform_noise(shape, 1e-3, seed=9) + 2e-3
+    p = drop_params(9, shape, phi=0.0, phi_field=phi, sbar=3.0)
+    run = make_run(p, R0=7)
+    r0, _, _ = totals(run)
+    run.step(1)
+    want = float(np.sum(phi[run.mask.astype(bool)]) / 3.0)
+    assert run.ledger.last_removed == pytest.approx(want, rel=1e-13)
+    r1, _, _ = totals(run)
+    assert (r0 - r1) == pytest.approx(want, rel=1e-10)
+
+
+@pytest.mark.parametrize("q,shape,periodic", [(9, (1, 20, 24), (1, 0, 1)),
+                                              (9, (1, 20, 24), (0, 0, 1)),
+                                              (19, (8, 10, 12), (1, 1, 0)),
+                                              (19, (8, 10, 12), (0, 1, 0))])
+def test_walls_conserve_mass(q, shape, periodic):
+    p = drop_params(q, shape, periodic=periodic, phi=1e-3)
+    run = make_run(p, R0=shape[1] / 3)
+    r0, b0, _ = totals(run)
+    run.step(40)
+    r1, b1, _ = totals(run)
+    assert abs((r1 + b1) - (r0 + b0)) <= 1e-13 * (r0 + b0)
+    assert abs((r0 - r1) - run.evaporated) <= 1e-12 * r0
+
+
+def test_solid_obstacle_conserves_mass():
+    shape = (1, 24, 28)
+    solid = np.zeros(shape, np.uint8)
+    solid[0, 10:14, 3:6] = 1
+    p = drop_params(9, shape, solid=solid, phi=1e-3)
+    run = make_run(p, R0=6)
+    f0 = run.f.copy()
+    assert np.all(f0[:, :, solid.astype(bool)] == 0)
+    r0, b0, _ = totals(run)
+    run.step(50)
+    r1, b1, _ = totals(run)
+    assert np.all(run.f[:, :, solid.astype(bool)] == 0)
+    assert abs((r1 + b1) - (r0 + b0)) <= 1e-13 * (r0 + b0)
+    assert abs((r0 - r1) - run.evaporated) <= 1e-12 * r0
+
+
+@pytest.mark.parametrize("q,n,steps", [(9, 22, 120), (19, 10, 20)])
+def test_mirror_symmetry_of_centred_drop(q, n, steps):
+    shape = (1, n, n) if q == 9 else (n, n, n)
+    p = drop_params(q, shape, phi=1e-3)
+    run = make_run(p, R0=n / 4, noise=0.0)
+    run.step(steps)
+    rr = run.macros()["rho_r"]
+    axes = (1, 2) if q == 9 else (0, 1, 2)
+    for ax in axes:
+        assert np.max(np.abs(rr - np.flip(rr, axis=ax))) < 1e-13
+    assert np.max(np.abs(rr - np.swapaxes(rr, 1, 2))) < 1e-13
+    if q == 19:
+        assert np.max(np.abs(rr - np.swapaxes(rr, 0, 1))) < 1e-13
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0, 1.4])
+def test_single_component_shear_wave(tau):
+    """All-red fluid, sigma = 0: the model is single-relaxation BGK; a shear wave
+    u_x = U sin(k y) decays at rate nu k^2 with nu = (tau - 1/2) / 3."""
+    L = 64
+    p = oracle.Params(q=9, nx=1, ny=L, nz=1, tau_r=tau, tau_b=tau, sigma=0.0, beta=0.7, phi=0.0)
+    lat = oracle.lattice(9)
+    k = 2 * np.pi / L
+    U = 1e-4
+    f = np.zeros((2, 9, 1, L, 1))
+    for y in range(L):
+        f[0, :, 0, y, 0] = oracle.feq(9, 1.0, [U * np.sin(k * y), 0, 0], lat["w"][0])
+    run = oracle.Run(p, f)
+    amp = []
+    steps = 400
+    for _ in range(steps // 50):
+        run.step(50)
+        ux = run.macros()["u"][0, 0, :, 0]
+        amp.append(2.0 / L * np.sum(ux * np.sin(k * np.arange(L))))
+    amp = np.array(amp)
+    t = 50.0 * np.arange(1, len(amp) + 1)
+    rate = -np.polyfit(t, np.log(amp), 1)[0]
+    nu = (tau - 0.5) / 3.0
+    assert rate == pytest.approx(nu * k * k, rel=2e-3)
+    assert np.all(run.macros()["rho_b"] == 0.0)
+
+
+@pytest.mark.slow
+def test_laplace_law_2d():
+    """Static drop, flux off: p_in - p_out = sigma / R (2D), p from Eq. (EOS)."""
+    sigma = 0.05
+    vals = []
+    for R0 in (10.0, 14.0, 18.0):
+        p = drop_params(9, (1, 64, 64), sigma=sigma, beta=0.99, phi=0.0)
+        run = make_run(p, R0=R0, noise=0.0)
+        run.step(3000)
+        m = run.macros()
+        L = oracle.lattice(9)
+        rn = m["rho_N"] if "rho_N" in m else m["rhoN"]
+        rho = m["rho_r"] + m["rho_b"]
+        p_in = rho[0, 31:33, 31:33].mean() * L["zeta"] * (1 - L["w"][0])
+        p_out = rho[0, 0:2, 0:2].mean() * L["zeta"] * (1 - L["w"][0])
+        R = np.sqrt(np.sum((1 + rn) / 2) / np.pi)
+        vals.append((p_in - p_out) * R / sigma)
+    vals = np.array(vals)
+    assert np.all(np.abs(vals - 1.0) < 0.08), vals
+    assert vals.max() - vals.min() < 0.05, vals
+
+
+def test_sampled_step_equals_full_step():
+    for q, shape, rule, per in [(9, (1, 13, 11), oracle.RULE_BAND, (1, 1, 1)),
+                                (19, (5, 7, 6), oracle.RULE_GRADIENT, (1, 0, 1))]:
+        p = drop_params(q, shape, site_rule=rule, threshold=0.3 if rule == 0 else 0.5,
+                        phi=1e-3, periodic=per)
+        run = make_run(p, R0=2.5)
+        run.step(3)
+        f, G = run.f.copy(), run.G.copy()
+        cells = np.arange(p.ncell)
+        of, oG, om = oracle.step_cells(p, f, G, cells)
+        run.step(1)
+        full = run.f.reshape(2, q, -1).transpose(2, 0, 1)
+        assert np.array_equal(of, full)
+        assert np.array_equal(oG, run.G.reshape(-1))
+        assert np.array_equal(om, run.mask.reshape(-1))
