@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of the fused colour-gradient LBM + reaction-limited evaporation step on GB300.
+
+Workload (default): D3Q19 spherical drop R0 = 32 in a 192^3 periodic box, density ratio 10,
+tau_l = 1, tau_g = 0.8, A = 0.005, beta = 0.7, phi = 1e-5, sites |rho^N| < 0.5, seeded
+U(+-1e-6) noise.  One bench step = one timestep of the whole lattice = one launch of the fused
+kernel.  The headline line is FP32 storage and arithmetic; FP16 / BF16 deviation storage
+(FP32 arithmetic) and FP64 run the same steps from the same initial state and report their
+speed and their error against the FP64 path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as N independent replicas (weak scaling, no data-path collective).
+`--impl reference` times the FP64 CPU oracle (the only reference this paper has) on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline, CG-LBM+evaporation step; mixed vs FP64 at stated error"
+UNIT = "MLUPS"
+KERNEL_SOURCES = ["lattice.cuh", "common.cuh", "step_kernel.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=192)
+    ap.add_argument("--storages", default="f32,f16dev,bf16dev,f64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing ------
+
+class Dist:
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(cells_per_rank: float, steps: int, ms_per_rank: float, d: Dist):
+    """Whole-job MLUPS: all ranks' lattice updates over the slowest rank's time."""
+    ms = d.max(ms_per_rank)
+    total = d.sum(cells_per_rank * steps)
+    return total / (ms / 1e3) / 1e6, ms
+
+
+# ------------------------------------------------------------------ measurement helpers -----
+
+class Clocks:
+    """nvidia-smi samples during a timed region (read only; no setting is changed)."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool = True):
+        self.idx = gpu_index
+        try:
+            import torch
+            gpu_index = "GPU-" + str(torch.cuda.get_device_properties(gpu_index).uuid)
+        except Exception:
+            pass
+        self.proc = None
+        self.path = None
+        if enabled:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except OSError:
+                self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2412_14859_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage: str, size: int):
+    """DRAM bytes per lattice update of the fused kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if kv.get("storage") == storage and kv.get("hash") == kernel_hash():
+            return float(kv["dram_bytes_per_cell"])
+    return None
+
+
+def workload(size: int):
+    from paper_2412_14859_gb300 import inputs
+    return inputs.sphere_3d(size, 32.0 * size / 192.0)
+
+
+def describe(case) -> str:
+    n = case.shape[0]
+    return (f"sphere_3d: D3Q19 {n}^3 periodic, drop R0={case.R0:g}, rho_l/rho_g="
+            f"{case.rho_r_in / case.rho_b_in:g}, tau_l={case.tau_r:g}, tau_g={case.tau_b:g}, "
+            f"A=0.005, beta={case.beta:g}, phi={case.phi:g}, sites |rho^N|<{case.threshold:g}, "
+            f"noise U(+-1e-6)")
+
+
+# ------------------------------------------------------------------ CPU oracle timing -------
+
+def oracle_rate(side: int, steps: int):
+    """MLUPS of the FP64 C oracle (single thread) on a side^3 box of the same physics."""
+    import oracle
+    from tests.harness import oracle_params
+    case = workload(side)
+    p = oracle_params(case)
+    run = oracle.Run(p, oracle.init(p, case.phase(), None))
+    t0 = time.perf_counter()
+    run.step(steps)
+    dt = time.perf_counter() - t0
+    return case.ncell * steps / dt / 1e6, dt
+
+
+def cpu_baseline(target_s: float = 12.0):
+    side = 64
+    rate, dt = oracle_rate(side, 1)
+    steps = max(1, min(100, int(target_s / max(dt, 1e-3))))
+    rate, dt = oracle_rate(side, steps)
+    return {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, one thread, {steps} steps of the same physics on a {side}^3 "
+                      f"box (drop R0={32 * side / 192:g}), {dt:.1f} s"}
+
+
+def run_reference(args, d: Dist):
+    if d.rank != 0:
+        return
+    import oracle
+    from tests.harness import oracle_params
+    # size the sample so warm-up + timed steps take about two minutes
+    probe, dt1 = oracle_rate(32, 1)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    side = int(max(12, min(args.size, round((budget * probe * 1e6) ** (1 / 3)))))
+    case = workload(side)
+    p = oracle_params(case)
+    run = oracle.Run(p, oracle.init(p, case.phase(), None))
+    run.step(args.warmup)
+    t0 = time.perf_counter()
+    run.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = case.ncell * args.steps / dt / 1e6
+    full = workload(args.size)
+    sample = (f"FP64 C oracle, one thread; each step is one timestep of the same physics on a "
+              f"{side}^3 box (drop R0={case.R0:g}) instead of {args.size}^3")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(full), "cells": full.ncell, "sample_cells": case.ncell},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU path -----------------
+
+def run_ours(args, d: Dist):
+    import numpy as np
+    import torch
+    from paper_2412_14859_gb300.binding import Sim
+    from paper_2412_14859_gb300 import inputs
+
+    torch.cuda.set_device(d.local_rank)
+    dev = torch.device("cuda", d.local_rank)
+    case = workload(args.size)
+    rn = torch.from_numpy(case.phase()).to(dev)
+    noise = torch.from_numpy(inputs.uniform_noise((2, 19) + case.shape, case.noise, case.seed,
+                                                  np.float32)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    storages = [s for s in args.storages.split(",") if s]
+    results, rho_r = {}, {}
+
+    for st in storages:
+        K = args.steps
+        with torch.cuda.stream(stream):
+            sim = Sim.from_case(case, st)
+            sim.set_flux(case.phi)
+            sim.init_equilibrium(rn, noise)
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            d.barrier()
+            clocks = Clocks(d.local_rank, enabled=(st == storages[0] and not args.no_clocks))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            d.barrier()
+            ms = e0.elapsed_time(e1)
+            mlups, ms_max = aggregate(sim.fluid_cells, K, ms, d)
+            bpu = sim.bytes_per_update
+            per_launch_s = ms / K / 1e3
+            achieved = bpu * sim.fluid_cells / per_launch_s / 1e9
+            m = sim.macros()
+            rho_r[st] = m["rho_r"]
+            led = sim.ledger()
+            results[st] = {"mlups": mlups, "ms": ms_max, "bytes_per_update": bpu,
+                           "achieved_gbs": achieved, "frac": achieved / hbm, "clocks": clk,
+                           "mass_r": float(m["rho_r"].sum()), "ledger": led["evaporated"],
+                           "steps_total": led["steps"], "sim": sim}
+        if st != storages[0]:
+            sim.close()
+            results[st]["sim"] = None
+
+    head = storages[0]
+    H = results[head]
+    ref = "f64" if "f64" in results else None
+    variants = {}
+    for st, r in results.items():
+        v = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms"] / args.steps, 4),
+             "bytes_per_update": r["bytes_per_update"], "hbm_gbs": round(r["achieved_gbs"], 1),
+             "hbm_frac": round(r["frac"], 4), "speedup_vs_f32": None}
+        if "f32" in results:
+            v["speedup_vs_f32"] = round(r["mlups"] / results["f32"]["mlups"], 3)
+        if ref and st != ref:
+            a, b = rho_r[st], rho_r[ref]
+            v["vs_f64"] = {
+                "steps": r["steps_total"],
+                "rel_mass_error_red": abs(r["mass_r"] - results[ref]["mass_r"]) / results[ref]["mass_r"],
+                "rel_linf_rho_r": float((a - b).abs().max() / b.abs().max()),
+                "rel_error_evaporated_ledger": abs(r["ledger"] - results[ref]["ledger"]) / max(results[ref]["ledger"], 1e-300),
+            }
+        variants[st] = v
+
+    # ---- end to end through the C ABI with host buffers (headline storage) -------------------
+    e2e = None
+    sim = H["sim"]
+    if not args.no_e2e:
+        with torch.cuda.stream(stream):
+            f_host = sim.populations(torch.float32).cpu().pin_memory().numpy()
+            sim.close()
+            sim2 = Sim.from_case(case, head)
+            sim2.set_flux(case.phi)
+            sim2.set_populations_host(f_host)  # allocates the staging buffer once, untimed
+            torch.cuda.synchronize()
+            d.barrier()
+            t0 = time.perf_counter()
+            sim2.set_populations_host(f_host)
+            for _ in range(args.steps):
+                sim2.step(1)
+                sim2.ledger()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            d.barrier()
+            e2e_mlups, _ = aggregate(sim2.fluid_cells, args.steps, dt * 1e3, d)
+            e2e = {"value": round(e2e_mlups, 1), "unit": UNIT,
+                   "h2d_bytes_per_step": int(f_host.nbytes // args.steps),
+                   "d2h_bytes_per_step": 40}
+            sim2.close()
+    elif sim is not None:
+        sim.close()
+
+    if d.rank != 0:
+        return
+    traffic = ncu_traffic(head, args.size)
+    cells = case.ncell
+    line = {
+        "metric": METRIC, "value": round(H["mlups"], 1), "unit": UNIT, "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(H["ms"] / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head if head != "f16dev" else "f32",
+        "data": "synthetic",
+        "config": {"workload": describe(case), "cells": cells, "storage": head,
+                   "parallelism": f"{d.world} independent replicas" if d.world > 1 else "1 GPU",
+                   "l2": "no flush: the state (2 x %.2f GB) is larger than L2" % (
+                       H["bytes_per_update"] * cells / 2 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": round(H["achieved_gbs"], 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(H["frac"], 4),
+                     "traffic": None if traffic is None else round(traffic * cells),
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_update": H["bytes_per_update"],
+                     "kernel": "cg_step_kernel (fused step)"},
+        "variants": variants,
+        "gpu_launches": args.steps,
+    }
+    if H["clocks"]:
+        line["clocks"] = H["clocks"]
+    if e2e:
+        line["e2e"] = e2e
+    if d.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) != args.gpus:
+        sys.exit("--gpus N > 1 must be launched with torchrun --nproc-per-node N")
+    if args.impl == "reference":
+        d = Dist("gloo")
+        try:
+            run_reference(args, d)
+        finally:
+            d.close()
+        return
+    d = Dist("nccl")
+    try:
+        run_ours(args, d)
+    finally:
+        d.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * cgevap.h -- C ABI of the GB300 (sm_103a) library for the two-component colour-gradient (CG)
+ * lattice Boltzmann step with reaction-limited (RL) evaporation of Nath, Aouane and Harting,
+ * "Reaction-limited evaporation for the color-gradient lattice Boltzmann model",
+ * arXiv:2412.14859.
+ *
+ * One timestep (cgevap_step) is one fused CUDA kernel performing, in the order of the method
+ * summary at the end of the paper's Sec. II.B:
+ *   streaming (Eq. Stream, pull form, halfway bounce-back at walls, Sec. III first paragraph),
+ *   site selection (|F| > Gamma with |F| of the previous step, Sec. II.B; or a phase-field band),
+ *   mass exchange of the rest populations f0^r -= varphi, f0^b += varphi (Eq. exchange) with
+ *   varphi = phi / S-bar (Eq. relation), moments, colour gradient (Eq. cg, isotropic stencil),
+ *   BGK collision with harmonic tau (Eq. collision, Eq. feq), perturbation (Eq. perturb) and
+ *   recoloring (Eq. recolor).  The evaporated mass is summed in FP64 on the device.
+ *
+ * Conventions for every function:
+ *   - return 0 (CGEVAP_OK) on success or a negative CGEVAP_ERR_* code; nothing throws, aborts or
+ *     exits across this boundary; cgevap_last_error(sim) gives a message for the last failure
+ *     on that handle (cgevap_last_error(NULL) for failures of cgevap_create);
+ *   - pointers named dev_* are CUDA device pointers owned by the caller, host_* host pointers;
+ *     inputs are copied into library-owned buffers, outputs are written into the caller's buffers;
+ *   - work is enqueued on the handle's stream (cgevap_set_stream) and is asynchronous unless the
+ *     function says it synchronises;
+ *   - field layouts are C order [z][y][x] with x fastest (nz = 1 for D2Q9); population arrays
+ *     exchanged with the caller are [k][i][z][y][x], k = 0 red (the evaporating liquid), 1 blue;
+ *   - the stored state is the post-recoloring population f_i^{k*} of the last completed step.
+ */
+#ifndef CGEVAP_H
+#define CGEVAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(CGEVAP_BUILD) && defined(__GNUC__)
+#define CGEVAP_API __attribute__((visibility("default")))
+#else
+#define CGEVAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CGEVAP_OK 0
+#define CGEVAP_ERR_ARG -1          /* invalid argument or parameter set                       */
+#define CGEVAP_ERR_CUDA -2         /* a CUDA runtime call or kernel launch failed             */
+#define CGEVAP_ERR_OOM -3          /* device or host allocation failed                        */
+#define CGEVAP_ERR_TIMEOUT -4      /* a bounded device-side wait gave up                      */
+#define CGEVAP_ERR_NAN -5          /* the health check found a non-finite or negative density */
+#define CGEVAP_ERR_UNSUPPORTED -6  /* valid request this build does not provide               */
+#define CGEVAP_ERR_IO -7           /* checkpoint file could not be read or written            */
+
+/* ---- evaporation-site rules ---- */
+#define CGEVAP_SITES_GRADIENT 0 /* site if |F| of the previous step > threshold (Sec. II.B)     */
+#define CGEVAP_SITES_BAND 1     /* site if |rho^N| after streaming < threshold (phase band)     */
+
+/* ---- population storage formats (internal layouts; all arithmetic as stated) ---- */
+#define CGEVAP_F64 0      /* FP64 storage, FP64 arithmetic                                     */
+#define CGEVAP_F32 1      /* FP32 storage, FP32 arithmetic                                     */
+#define CGEVAP_F16DEV 2   /* FP32 rest populations + FP16 deviations of the moving ones, FP32 */
+#define CGEVAP_BF16DEV 3  /* as F16DEV with BF16 deviations                                    */
+
+/* ---- element types of caller buffers ---- */
+#define CGEVAP_DTYPE_F64 0
+#define CGEVAP_DTYPE_F32 1
+
+typedef struct cgevap_params {
+  int q;                  /* 9 (D2Q9, nz == 1) or 19 (D3Q19)                                  */
+  int nx, ny, nz;         /* lattice size, each >= 1; nx*ny*nz < 2^31                          */
+  int periodic[3];        /* per axis x,y,z: 1 periodic, 0 walls just outside both ends        */
+  double rho_r_in;        /* initial bulk density of red; alpha_k from these (Sec. II.A)      */
+  double rho_b_in;        /* initial bulk density of blue                                     */
+  double tau_r, tau_b;    /* component relaxation times, > 1/2 (Sec. II.A)                    */
+  double sigma;           /* surface tension; perturbation amplitude (9/4) sigma / tau        */
+  double beta;            /* recoloring parameter in [0, 1] (Eq. recolor)                     */
+  int site_rule;          /* CGEVAP_SITES_GRADIENT or CGEVAP_SITES_BAND                        */
+  double threshold;       /* Gamma (gradient rule) or theta (band rule)                       */
+  double sbar;            /* S-bar > 0 of Eq. (relation); varphi = phi / S-bar                */
+  int storage;            /* CGEVAP_F64, CGEVAP_F32, CGEVAP_F16DEV or CGEVAP_BF16DEV          */
+} cgevap_params;
+
+typedef struct cgevap_ledger {
+  double evaporated;      /* cumulative FP64 sum of varphi over (site, step) pairs             */
+  double last_removed;    /* FP64 sum of varphi over the sites of the last step                */
+  long long site_steps;   /* cumulative number of (site, step) pairs                           */
+  long long last_sites;   /* number of sites at the last step                                  */
+  long long steps;        /* steps taken since create / reset / load                           */
+} cgevap_ledger;
+
+typedef struct cgevap_sim cgevap_sim;
+
+/* Validate p and allocate a simulation on the current CUDA device: two population buffers, two
+ * site-mask buffers, the FP64 ledger and its per-block scratch.  Populations start at zero, the
+ * flux at zero, the stream is the legacy default stream.  Errors: ARG (invalid p: q not 9/19,
+ * nz != 1 with q = 9, a size < 1, tau <= 1/2, beta outside [0,1], densities or S-bar <= 0,
+ * unknown rule or storage), OOM, CUDA.  *out is NULL on failure. */
+CGEVAP_API int cgevap_create(const cgevap_params* p, cgevap_sim** out);
+
+/* Synchronise the handle's stream and free everything it owns.  NULL is accepted. */
+CGEVAP_API int cgevap_destroy(cgevap_sim* sim);
+
+/* Message for the last failure on sim (or of cgevap_create when sim is NULL); never NULL. */
+CGEVAP_API const char* cgevap_last_error(const cgevap_sim* sim);
+
+/* Parameters the handle was created with. */
+CGEVAP_API int cgevap_get_params(const cgevap_sim* sim, cgevap_params* out);
+
+/* Enqueue all later work on this cudaStream_t (NULL = legacy default stream). */
+CGEVAP_API int cgevap_set_stream(cgevap_sim* sim, void* cuda_stream);
+
+/* Copy a per-cell solid flag (uint8, nonzero = solid, [z][y][x]) or clear it (dev_solid NULL).
+ * Solid cells hold no populations; fluid links into them bounce back halfway (Sec. III) and
+ * they contribute the evaluating cell's rho^N to the colour gradient (neutral wetting).
+ * Populations of cells that become solid are zeroed. */
+CGEVAP_API int cgevap_set_solid(cgevap_sim* sim, const uint8_t* dev_solid);
+
+/* Evaporative flux phi (Eq. surface_flux): a scalar (dev_phi_field NULL) or a per-cell field
+ * [z][y][x] of dtype CGEVAP_DTYPE_F64/F32 that is copied.  Each site loses varphi = phi / S-bar
+ * of red rest population per step (Eq. relation, Eq. exchange); negative phi condenses. */
+CGEVAP_API int cgevap_set_flux(cgevap_sim* sim, double phi, const void* dev_phi_field, int dtype);
+
+/* Initial state at rest: rho_r = rho_r_in (1 + rhoN0) / 2, rho_b = rho_b_in (1 - rhoN0) / 2,
+ * f_i^k = rho_k phi_i(alpha_k) (Eq. feq with u = 0) plus dev_noise [k][i][z][y][x] if not NULL
+ * (dtype noise_dtype).  dev_rhoN0 is FP64 [z][y][x].  Also resets the ledger and, for the
+ * gradient rule, sets the first step's sites from |F| of this state. */
+CGEVAP_API int cgevap_init_equilibrium(cgevap_sim* sim, const double* dev_rhoN0, const void* dev_noise,
+                            int noise_dtype);
+
+/* Replace the state by dev_f [k][i][z][y][x] (dtype F64 or F32), encoded into the storage
+ * format; recomputes the gradient-rule sites of the next step from this state. */
+CGEVAP_API int cgevap_set_populations(cgevap_sim* sim, const void* dev_f, int dtype);
+/* Same from host memory (pageable or pinned); synchronises the stream. */
+CGEVAP_API int cgevap_set_populations_host(cgevap_sim* sim, const void* host_f, int dtype);
+
+/* Decode the state into dev_f [k][i][z][y][x] (dtype F64 or F32). */
+CGEVAP_API int cgevap_get_populations(cgevap_sim* sim, void* dev_f, int dtype);
+
+/* Advance nsteps >= 0 timesteps (asynchronous; the ledger is updated on the device). */
+CGEVAP_API int cgevap_step(cgevap_sim* sim, int nsteps);
+
+/* Local macroscopic fields of the state (FP64, each [z][y][x], u is [3][z][y][x]); any pointer
+ * may be NULL.  rho_k = sum_i f_i^k, u = sum_i f_i c_i / rho, rho^N = (rho_r - rho_b) / rho
+ * (Sec. II.A); these equal the post-exchange moments of the last step. Solid cells give 0. */
+CGEVAP_API int cgevap_get_macros(cgevap_sim* sim, double* dev_rho_r, double* dev_rho_b, double* dev_u,
+                      double* dev_rhoN);
+
+/* Site byte per cell [z][y][x] of the last step: bit0 = site at that step, bit1 = gradient
+ * rule: |F| > Gamma at that step (site at the next one), bit2 = that step's decision value lay
+ * within 1e-6 of the threshold, bit3 = gradient rule: | |F| - Gamma | < 1e-6 at that step. */
+CGEVAP_API int cgevap_get_mask(cgevap_sim* sim, uint8_t* dev_mask);
+
+/* Copy the FP64 ledger to the host; synchronises the stream. */
+CGEVAP_API int cgevap_get_ledger(cgevap_sim* sim, cgevap_ledger* host_out);
+
+/* Zero the ledger (asynchronous). */
+CGEVAP_API int cgevap_reset_ledger(cgevap_sim* sim);
+
+/* Health check: CGEVAP_ERR_NAN if any fluid cell has a non-finite population or a non-positive
+ * total density, else OK; synchronises the stream. */
+CGEVAP_API int cgevap_check_health(cgevap_sim* sim);
+
+/* Write / read a checkpoint: a versioned header, the parameters, the state decoded to FP64,
+ * the site bytes, the flux, the solid flags and the ledger.  Loading needs a handle created
+ * with the same parameters; running n steps, saving, loading and running m more equals
+ * running n + m steps bit for bit.  Both synchronise the stream. Errors: IO, ARG. */
+CGEVAP_API int cgevap_save(cgevap_sim* sim, const char* path);
+CGEVAP_API int cgevap_load(cgevap_sim* sim, const char* path);
+
+/* Bytes the algorithm must move per lattice update of this handle's fused step (populations
+ * read and written, site byte read and/or written, flux field read); the numerator of the HBM
+ * roofline fraction. */
+CGEVAP_API double cgevap_bytes_per_update(const cgevap_sim* sim);
+
+/* Number of fluid cells. */
+CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGEVAP_H */

@@ -113,28 +113,34 @@ void orc_alphas(const orc_params *p, double *alpha_r, double *alpha_b) {
   *alpha_b = (p->rho_b_in <= rmin) ? w0 : 1.0 - (1.0 - w0) / (p->rho_b_in / rmin);
 }
 
-void orc_feq(int q, double rho, const double *u, double abar, double *feq) {
-  lattice L;
-  make_lattice(q, &L);
+static void feq_on(const lattice *L, double rho, const double *u, double abar, double *feq) {
   double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  for (int i = 0; i < q; i++) {
-    double cu = L.c[i][0] * u[0] + L.c[i][1] * u[1] + L.c[i][2] * u[2];
-    feq[i] = rho * (L.a[i] + L.b[i] * abar + L.w[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+  for (int i = 0; i < L->Q; i++) {
+    double cu = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
+    feq[i] = rho * (L->a[i] + L->b[i] * abar + L->w[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
   }
 }
 
-void orc_perturbation_shape(int q, const double *F, double *out) {
-  lattice L;
-  make_lattice(q, &L);
+static void perturbation_on(const lattice *L, const double *F, double *out) {
   double Fn = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
-  for (int i = 0; i < q; i++) {
+  for (int i = 0; i < L->Q; i++) {
     if (Fn == 0.0) {
       out[i] = 0.0;
       continue;
     }
-    double Fc = F[0] * L.c[i][0] + F[1] * L.c[i][1] + F[2] * L.c[i][2];
-    out[i] = Fn * (L.w[i] * Fc * Fc / (Fn * Fn) - L.cw[i]);
+    double Fc = F[0] * L->c[i][0] + F[1] * L->c[i][1] + F[2] * L->c[i][2];
+    out[i] = Fn * (L->w[i] * Fc * Fc / (Fn * Fn) - L->cw[i]);
   }
+}
+
+void orc_feq(int q, double rho, const double *u, double abar, double *feq) {
+  lattice L;
+  if (make_lattice(q, &L)) feq_on(&L, rho, u, abar, feq);
+}
+
+void orc_perturbation_shape(int q, const double *F, double *out) {
+  lattice L;
+  if (make_lattice(q, &L)) perturbation_on(&L, F, out);
 }
 
 /* ---------------------------------------------------------------- geometry -------------- */
@@ -255,11 +261,11 @@ static void collide_cell(const orc_params *p, const lattice *L, double alpha_r, 
   double abar = wr * alpha_r + wb * alpha_b;
 
   double feq[QMAX];
-  orc_feq(Q, rho, u, abar, feq);
+  feq_on(L, rho, u, abar, feq);
   for (int i = 0; i < Q; i++) f[i] = f[i] - inv_tau * (f[i] - feq[i]); /* Eq. (collision) */
 
   double shape[QMAX];
-  orc_perturbation_shape(Q, F, shape);
+  perturbation_on(L, F, shape);
   for (int i = 0; i < Q; i++) f[i] += 2.25 * p->sigma * inv_tau * shape[i]; /* Eq. (perturb) */
 
   double Fn = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);

@@ -1,0 +1,248 @@
+"""ctypes binding of libcgevap.so (include/cgevap.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch provides device memory (tensors
+whose data pointers are passed through) and the current CUDA stream.  ``lib()`` raises if the
+library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcgevap.so")
+
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
+DTYPE_F64, DTYPE_F32 = 0, 1
+SITES_GRADIENT, SITES_BAND = 0, 1
+ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NAN", -6: "UNSUPPORTED", -7: "IO"}
+
+
+class CgevapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"cgevap error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("q", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
+        ("rho_r_in", ctypes.c_double), ("rho_b_in", ctypes.c_double),
+        ("tau_r", ctypes.c_double), ("tau_b", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
+        ("site_rule", ctypes.c_int), ("threshold", ctypes.c_double), ("sbar", ctypes.c_double),
+        ("storage", ctypes.c_int),
+    ]
+
+
+class Ledger(ctypes.Structure):
+    _fields_ = [
+        ("evaporated", ctypes.c_double), ("last_removed", ctypes.c_double),
+        ("site_steps", ctypes.c_longlong), ("last_sites", ctypes.c_longlong),
+        ("steps", ctypes.c_longlong),
+    ]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_SIGS = {
+    "cgevap_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+    "cgevap_destroy": (ctypes.c_int, [_vp]),
+    "cgevap_last_error": (ctypes.c_char_p, [_vp]),
+    "cgevap_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(Params)]),
+    "cgevap_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_set_solid": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_set_flux": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.c_int]),
+    "cgevap_init_equilibrium": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "cgevap_set_populations": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "cgevap_set_populations_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "cgevap_get_populations": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "cgevap_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cgevap_get_macros": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "cgevap_get_mask": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_get_ledger": (ctypes.c_int, [_vp, ctypes.POINTER(Ledger)]),
+    "cgevap_reset_ledger": (ctypes.c_int, [_vp]),
+    "cgevap_check_health": (ctypes.c_int, [_vp]),
+    "cgevap_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "cgevap_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "cgevap_bytes_per_update": (ctypes.c_double, [_vp]),
+    "cgevap_fluid_cells": (ctypes.c_longlong, [_vp]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcgevap.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return DTYPE_F64
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    raise ValueError(f"unsupported dtype {t.dtype}")
+
+
+class Sim:
+    """One lattice on the current CUDA device (a handle of the C ABI)."""
+
+    def __init__(self, q: int, nx: int, ny: int, nz: int = 1, periodic=(1, 1, 1),
+                 rho_r_in: float = 1.0, rho_b_in: float = 1.0, tau_r: float = 1.0,
+                 tau_b: float = 1.0, sigma: float = 0.0, beta: float = 0.7,
+                 site_rule: int = SITES_BAND, threshold: float = 0.5, sbar: float = 3.0,
+                 storage="f32"):
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.params = Params(q, nx, ny, nz, (ctypes.c_int * 3)(*periodic), rho_r_in, rho_b_in,
+                             tau_r, tau_b, sigma, beta, site_rule, threshold, sbar, st)
+        self.q, self.shape = q, (nz, ny, nx)
+        self.ncell = nx * ny * nz
+        h = _vp()
+        rc = lib().cgevap_create(ctypes.byref(self.params), ctypes.byref(h))
+        if rc != 0:
+            raise CgevapError(rc, lib().cgevap_last_error(None).decode())
+        self._h = h
+        self._sync_stream()
+
+    @classmethod
+    def from_case(cls, case, storage="f32") -> "Sim":
+        nz, ny, nx = case.shape
+        return cls(case.q, nx, ny, nz, case.periodic, case.rho_r_in, case.rho_b_in, case.tau_r, case.tau_b,
+                   case.sigma, case.beta, case.site_rule, case.threshold, case.sbar, storage)
+
+    # -- plumbing -----------------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise CgevapError(rc, lib().cgevap_last_error(self._h).decode())
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream().cuda_stream
+        self._check(lib().cgevap_set_stream(self._h, s))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cgevap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- inputs ---------------------------------------------------------------------------------
+    def set_flux(self, phi: float, field: Optional[torch.Tensor] = None):
+        self._sync_stream()
+        self._check(lib().cgevap_set_flux(self._h, float(phi), _ptr(field),
+                                          _dt(field) if field is not None else 0))
+
+    def set_solid(self, solid: Optional[torch.Tensor]):
+        self._sync_stream()
+        self._check(lib().cgevap_set_solid(self._h, _ptr(solid, torch.uint8)))
+
+    def init_equilibrium(self, rhoN0: torch.Tensor, noise: Optional[torch.Tensor] = None):
+        self._sync_stream()
+        self._check(lib().cgevap_init_equilibrium(self._h, _ptr(rhoN0, torch.float64),
+                                                  _ptr(noise), _dt(noise) if noise is not None else 0))
+
+    def set_populations(self, f: torch.Tensor):
+        self._sync_stream()
+        self._check(lib().cgevap_set_populations(self._h, _ptr(f), _dt(f)))
+
+    def set_populations_host(self, f: np.ndarray):
+        if not f.flags.c_contiguous or f.dtype not in (np.float64, np.float32):
+            raise ValueError("expected a C-contiguous float64/float32 array")
+        self._sync_stream()
+        dt = DTYPE_F64 if f.dtype == np.float64 else DTYPE_F32
+        self._check(lib().cgevap_set_populations_host(self._h, f.ctypes.data, dt))
+
+    # -- stepping -------------------------------------------------------------------------------
+    def step(self, n: int = 1):
+        self._sync_stream()
+        self._check(lib().cgevap_step(self._h, int(n)))
+        return self
+
+    # -- outputs --------------------------------------------------------------------------------
+    def populations(self, dtype=torch.float64) -> torch.Tensor:
+        out = torch.empty((2, self.q) + self.shape, dtype=dtype, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_get_populations(self._h, out.data_ptr(), _dt(out)))
+        return out
+
+    def macros(self) -> dict:
+        rr, rb, rn = (torch.empty(self.shape, dtype=torch.float64, device="cuda") for _ in range(3))
+        u = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_get_macros(self._h, rr.data_ptr(), rb.data_ptr(), u.data_ptr(),
+                                            rn.data_ptr()))
+        return {"rho_r": rr, "rho_b": rb, "u": u, "rhoN": rn}
+
+    def mask(self) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.uint8, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_get_mask(self._h, out.data_ptr()))
+        return out
+
+    def ledger(self) -> dict:
+        L = Ledger()
+        self._sync_stream()
+        self._check(lib().cgevap_get_ledger(self._h, ctypes.byref(L)))
+        return {k: getattr(L, k) for k, _ in Ledger._fields_}
+
+    def reset_ledger(self):
+        self._sync_stream()
+        self._check(lib().cgevap_reset_ledger(self._h))
+
+    def check_health(self):
+        self._sync_stream()
+        self._check(lib().cgevap_check_health(self._h))
+
+    def save(self, path: str):
+        self._sync_stream()
+        self._check(lib().cgevap_save(self._h, path.encode()))
+
+    def load(self, path: str):
+        self._sync_stream()
+        self._check(lib().cgevap_load(self._h, path.encode()))
+
+    @property
+    def bytes_per_update(self) -> float:
+        return lib().cgevap_bytes_per_update(self._h)
+
+    @property
+    def fluid_cells(self) -> int:
+        return lib().cgevap_fluid_cells(self._h)
+
+
+def all_signatures():
+    """Names of the C functions this binding declares (kept equal to include/*.h by a test)."""
+    return list(_SIGS)

@@ -1,0 +1,624 @@
+// api.cu -- the C ABI of include/cgevap.h: handle lifetime, validation, launch planning and the
+// host side of every entry point.  No C++ exception or abort crosses the boundary.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cgevap.h"
+#include "launch.h"
+
+using namespace cgevap;
+
+struct cgevap_sim {
+  cgevap_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int Q = 0;
+  long long N = 0;
+  long long nfluid = 0;
+  Geom geom{};
+  Physics ph{};
+  size_t state_bytes = 0;
+  void* state[2] = {nullptr, nullptr};
+  uint8_t* mask[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t* links = nullptr;
+  uint8_t* solid = nullptr;
+  void* phi_field = nullptr;  // double (F64 storage) or float, [N]
+  double phi = 0.0;
+  DevLedger* ledger = nullptr;
+  double* part_removed = nullptr;
+  long long* part_sites = nullptr;
+  unsigned int* done = nullptr;
+  long long part_capacity = 0;
+  double* tmp_rn = nullptr;
+  int* flag = nullptr;
+  void* staging = nullptr;  // device staging for host imports
+  size_t staging_bytes = 0;
+  // launch plan of the fused step
+  int variant = 0;
+  KernelRef kernel{nullptr, 0};
+  int ntx = 1, nty = 1, pc = 1, nchunk = 1;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(cgevap_sim* s, int code, const std::string& msg) {
+  if (s)
+    s->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+#define CG_CUDA(s, call)                                                                 \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((s), CGEVAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+double w0_of(int q) { return q == 19 ? Lattice<19>::W(0) : Lattice<9>::W(0); }
+
+std::string validate(const cgevap_params* p) {
+  if (!p) return "params is NULL";
+  if (p->q != 9 && p->q != 19) return "q must be 9 or 19";
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "sizes must be >= 1";
+  if (p->q == 9 && p->nz != 1) return "D2Q9 needs nz == 1";
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return "nx*ny*nz must be < 2^31";
+  for (int d = 0; d < 3; ++d)
+    if (p->periodic[d] != 0 && p->periodic[d] != 1) return "periodic flags must be 0 or 1";
+  if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) return "tau_r and tau_b must be > 1/2";
+  if (!(p->rho_r_in > 0.0) || !(p->rho_b_in > 0.0)) return "initial densities must be > 0";
+  if (!(p->beta >= 0.0 && p->beta <= 1.0)) return "beta must lie in [0, 1]";
+  if (!(p->sbar > 0.0)) return "sbar must be > 0";
+  if (!std::isfinite(p->sigma) || !std::isfinite(p->threshold)) return "sigma/threshold not finite";
+  if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND)
+    return "unknown site rule";
+  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16DEV) return "unknown storage";
+  return "";
+}
+
+template <int Q>
+void fill_kappa(Physics& ph) {
+  using L = Lattice<Q>;
+  for (int i = 0; i < 19; ++i) {
+    ph.kap_r[i] = ph.kap_b[i] = 0.0f;
+    if (i < Q) {
+      ph.kap_r[i] = (float)((L::A(i) + L::B(i) * ph.alpha_r) / ph.alpha_r);
+      ph.kap_b[i] = (float)((L::A(i) + L::B(i) * ph.alpha_b) / ph.alpha_b);
+    }
+  }
+}
+
+void setup_physics(cgevap_sim* s) {
+  const cgevap_params& p = s->p;
+  Physics& ph = s->ph;
+  const double w0 = w0_of(p.q);
+  const double rmin = std::fmin(p.rho_r_in, p.rho_b_in);
+  // Sec. II.A: alpha = W_0 for the least dense component, 1 - (1 - W_0)/gamma_k otherwise.
+  ph.alpha_r = (p.rho_r_in <= rmin) ? w0 : 1.0 - (1.0 - w0) / (p.rho_r_in / rmin);
+  ph.alpha_b = (p.rho_b_in <= rmin) ? w0 : 1.0 - (1.0 - w0) / (p.rho_b_in / rmin);
+  ph.inv_tau_r = 1.0 / p.tau_r;
+  ph.inv_tau_b = 1.0 / p.tau_b;
+  ph.amp = 2.25 * p.sigma;
+  ph.beta = p.beta;
+  ph.rule = p.site_rule;
+  ph.threshold = p.threshold;
+  ph.inv_sbar = 1.0 / p.sbar;
+  ph.varphi = s->phi / p.sbar;
+  ph.phi_field = s->phi_field;
+  if (p.q == 19)
+    fill_kappa<19>(ph);
+  else
+    fill_kappa<9>(ph);
+  if (p.storage == CGEVAP_F16DEV) {
+    const double rmax = std::fmax(p.rho_r_in, p.rho_b_in);
+    int e = (int)std::floor(std::log2(16384.0 / rmax));
+    if (e > 10) e = 10;
+    if (e < 0) e = 0;
+    ph.scale = std::ldexp(1.0f, e);
+  } else {
+    ph.scale = 1.0f;
+  }
+  ph.inv_scale = 1.0f / ph.scale;
+}
+
+AuxArgs aux_of(const cgevap_sim* s) {
+  AuxArgs a;
+  a.g = s->geom;
+  a.ph = s->ph;
+  a.q = s->p.q;
+  a.storage = s->p.storage;
+  a.rho_r_in = s->p.rho_r_in;
+  a.rho_b_in = s->p.rho_b_in;
+  return a;
+}
+
+KernelRef kernel_for(int q, int storage, int variant) {
+  switch (storage) {
+    case CGEVAP_F64: return step_kernel_f64(q, variant);
+    case CGEVAP_F32: return step_kernel_f32(q, variant);
+    default: return step_kernel_dev(q, storage, variant);
+  }
+}
+
+// Planes per chunk: balance whole waves of resident CTAs against the two extra planes each
+// chunk pulls (time ~ waves * (pc + 2)).
+int plan_launch(cgevap_sim* s, int variant) {
+  const TileCfg t = tile_cfg(s->p.q, variant);
+  KernelRef k = kernel_for(s->p.q, s->p.storage, variant);
+  if (!k.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
+  int occ = 0, sms = 0;
+  CG_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, 0));
+  CG_CUDA(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+  if (occ < 1) occ = 1;
+  const int na = s->geom.na, nb = s->geom.nb, nm = s->geom.nm;
+  const int ntx = (na + t.tx - 1) / t.tx;
+  const int nty = (nb + t.ty - 1) / t.ty;
+  const long long tiles = (long long)ntx * nty;
+  const long long slots = (long long)occ * sms;
+  int best_pc = nm;
+  double best = 1e300;
+  for (int pc = 1; pc <= nm; ++pc) {
+    const long long nchunk = (nm + pc - 1) / pc;
+    if (nchunk > 65535) continue;
+    const long long blocks = tiles * nchunk;
+    const double waves = std::ceil((double)blocks / (double)slots);
+    const double cost = waves * (pc + 2);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_pc = pc;
+    }
+  }
+  s->variant = variant;
+  s->kernel = k;
+  s->ntx = ntx;
+  s->nty = nty;
+  s->pc = best_pc;
+  s->nchunk = (nm + best_pc - 1) / best_pc;
+  const long long need = tiles * s->nchunk;
+  if (need > s->part_capacity) {
+    if (s->part_removed) cudaFree(s->part_removed);
+    if (s->part_sites) cudaFree(s->part_sites);
+    s->part_removed = nullptr;
+    s->part_sites = nullptr;
+    if (cudaMalloc(&s->part_removed, need * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->part_sites, need * sizeof(long long)) != cudaSuccess) {
+      s->part_capacity = 0;
+      return fail(s, CGEVAP_ERR_OOM, "cannot allocate per-block partials");
+    }
+    s->part_capacity = need;
+  }
+  return CGEVAP_OK;
+}
+
+int launch_one_step(cgevap_sim* s) {
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = s->geom;
+  a.ph = s->ph;
+  a.red.part_removed = s->part_removed;
+  a.red.part_sites = s->part_sites;
+  a.red.done = s->done;
+  a.red.ledger = s->ledger;
+  a.ntx = s->ntx;
+  a.nty = s->nty;
+  a.pc = s->pc;
+  a.pin = s->state[s->cur];
+  a.pout = s->state[s->cur ^ 1];
+  a.mask_in = s->mask[s->cur];
+  a.mask_out = s->mask[s->cur ^ 1];
+  void* args[] = {&a};
+  CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
+                              dim3(s->kernel.threads), args, 0, s->stream));
+  s->cur ^= 1;
+  return CGEVAP_OK;
+}
+
+int refresh_gradient_sites(cgevap_sim* s) {
+  if (s->p.site_rule != CGEVAP_SITES_GRADIENT) {
+    CG_CUDA(s, cudaMemsetAsync(s->mask[s->cur], 0, s->N, s->stream));
+    return CGEVAP_OK;
+  }
+  if (!s->tmp_rn && cudaMalloc(&s->tmp_rn, s->N * sizeof(double)) != cudaSuccess)
+    return fail(s, CGEVAP_ERR_OOM, "cannot allocate rho^N scratch");
+  CG_CUDA(s, launch_gradient_sites(aux_of(s), s->state[s->cur], s->tmp_rn, s->mask[s->cur], s->stream));
+  return CGEVAP_OK;
+}
+
+void release(cgevap_sim* s) {
+  if (!s) return;
+  void* ptrs[] = {s->state[0], s->state[1], s->mask[0],  s->mask[1],  s->links,
+                  s->solid,    s->phi_field, s->ledger, s->part_removed, s->part_sites,
+                  s->done,     s->tmp_rn,   s->flag,    s->staging};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cgevap_create(const cgevap_params* p, cgevap_sim** out) {
+  if (!out) return fail(nullptr, CGEVAP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why = validate(p);
+  if (!why.empty()) return fail(nullptr, CGEVAP_ERR_ARG, why);
+  cgevap_sim* s = new (std::nothrow) cgevap_sim();
+  if (!s) return fail(nullptr, CGEVAP_ERR_OOM, "host allocation failed");
+  s->p = *p;
+  s->Q = p->q;
+  s->N = (long long)p->nx * p->ny * p->nz;
+  s->nfluid = s->N;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    release(s);
+    return fail(nullptr, CGEVAP_ERR_CUDA, "no CUDA device");
+  }
+  Geom& g = s->geom;
+  g.na = p->nx;
+  if (p->q == 19) {
+    g.nb = p->ny;
+    g.nm = p->nz;
+    g.per_a = p->periodic[0];
+    g.per_b = p->periodic[1];
+    g.per_m = p->periodic[2];
+  } else {
+    g.nb = 1;
+    g.nm = p->ny;
+    g.per_a = p->periodic[0];
+    g.per_b = 1;
+    g.per_m = p->periodic[1];
+  }
+  g.ncell = (int)s->N;
+  g.links = nullptr;
+  setup_physics(s);
+  s->state_bytes = state_bytes(p->storage, p->q, s->N);
+  bool ok = true;
+  for (int h = 0; h < 2 && ok; ++h) {
+    ok = cudaMalloc(&s->state[h], s->state_bytes) == cudaSuccess &&
+         cudaMalloc(&s->mask[h], s->N) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&s->ledger, sizeof(DevLedger)) == cudaSuccess &&
+       cudaMalloc(&s->done, sizeof(unsigned int)) == cudaSuccess &&
+       cudaMalloc(&s->flag, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    release(s);
+    return fail(nullptr, CGEVAP_ERR_OOM, "device allocation failed");
+  }
+  bool z = cudaMemset(s->state[0], 0, s->state_bytes) == cudaSuccess &&
+           cudaMemset(s->state[1], 0, s->state_bytes) == cudaSuccess &&
+           cudaMemset(s->mask[0], 0, s->N) == cudaSuccess &&
+           cudaMemset(s->mask[1], 0, s->N) == cudaSuccess &&
+           cudaMemset(s->ledger, 0, sizeof(DevLedger)) == cudaSuccess &&
+           cudaMemset(s->done, 0, sizeof(unsigned int)) == cudaSuccess;
+  if (!z) {
+    release(s);
+    return fail(nullptr, CGEVAP_ERR_CUDA, "initial memset failed");
+  }
+  int rc = plan_launch(s, 0);
+  if (rc != CGEVAP_OK) {
+    std::string m = s->err;
+    release(s);
+    return fail(nullptr, rc, m);
+  }
+  *out = s;
+  return CGEVAP_OK;
+}
+
+int cgevap_destroy(cgevap_sim* s) {
+  if (!s) return CGEVAP_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  release(s);
+  return CGEVAP_OK;
+}
+
+const char* cgevap_last_error(const cgevap_sim* s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int cgevap_get_params(const cgevap_sim* s, cgevap_params* out) {
+  if (!s || !out) return CGEVAP_ERR_ARG;
+  *out = s->p;
+  return CGEVAP_OK;
+}
+
+int cgevap_set_stream(cgevap_sim* s, void* stream) {
+  if (!s) return CGEVAP_ERR_ARG;
+  s->stream = (cudaStream_t)stream;
+  return CGEVAP_OK;
+}
+
+int cgevap_set_solid(cgevap_sim* s, const uint8_t* dev_solid) {
+  if (!s) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  if (!dev_solid) {
+    if (s->links) cudaFree(s->links);
+    if (s->solid) cudaFree(s->solid);
+    s->links = nullptr;
+    s->solid = nullptr;
+    s->geom.links = nullptr;
+    s->nfluid = s->N;
+    return CGEVAP_OK;
+  }
+  if (!s->solid && cudaMalloc(&s->solid, s->N) != cudaSuccess)
+    return fail(s, CGEVAP_ERR_OOM, "cannot allocate solid flags");
+  if (!s->links && cudaMalloc(&s->links, s->N * sizeof(uint32_t)) != cudaSuccess)
+    return fail(s, CGEVAP_ERR_OOM, "cannot allocate solid links");
+  CG_CUDA(s, cudaMemcpyAsync(s->solid, dev_solid, s->N, cudaMemcpyDeviceToDevice, s->stream));
+  Geom g = s->geom;
+  g.links = nullptr;
+  AuxArgs a = aux_of(s);
+  a.g = g;
+  CG_CUDA(s, launch_links(a, s->solid, s->links, s->stream));
+  s->geom.links = s->links;
+  CG_CUDA(s, launch_zero_solid(aux_of(s), s->state[s->cur], s->stream));
+  std::vector<uint8_t> h(s->N);
+  CG_CUDA(s, cudaMemcpyAsync(h.data(), s->solid, s->N, cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  long long nf = 0;
+  for (uint8_t v : h) nf += v ? 0 : 1;
+  s->nfluid = nf;
+  return refresh_gradient_sites(s);
+}
+
+int cgevap_set_flux(cgevap_sim* s, double phi, const void* dev_phi_field, int dtype) {
+  if (!s) return CGEVAP_ERR_ARG;
+  if (!std::isfinite(phi)) return fail(s, CGEVAP_ERR_ARG, "phi is not finite");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  s->phi = phi;
+  if (dev_phi_field) {
+    if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
+      return fail(s, CGEVAP_ERR_ARG, "flux dtype must be F64 or F32");
+    const bool dbl = s->p.storage == CGEVAP_F64;
+    if (!s->phi_field && cudaMalloc(&s->phi_field, s->N * (dbl ? 8 : 4)) != cudaSuccess)
+      return fail(s, CGEVAP_ERR_OOM, "cannot allocate flux field");
+    CG_CUDA(s, launch_convert_field(dev_phi_field, dtype, s->phi_field, dbl ? 1 : 0, s->N, s->stream));
+  } else if (s->phi_field) {
+    cudaFree(s->phi_field);
+    s->phi_field = nullptr;
+  }
+  s->ph.varphi = phi / s->p.sbar;
+  s->ph.phi_field = dev_phi_field ? s->phi_field : nullptr;
+  return CGEVAP_OK;
+}
+
+int cgevap_init_equilibrium(cgevap_sim* s, const double* dev_rhoN0, const void* dev_noise,
+                            int noise_dtype) {
+  if (!s || !dev_rhoN0) return CGEVAP_ERR_ARG;
+  if (dev_noise && noise_dtype != CGEVAP_DTYPE_F64 && noise_dtype != CGEVAP_DTYPE_F32)
+    return fail(s, CGEVAP_ERR_ARG, "noise dtype must be F64 or F32");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, launch_init_equilibrium(aux_of(s), dev_rhoN0, dev_noise, noise_dtype,
+                                     s->state[s->cur], s->stream));
+  CG_CUDA(s, cudaMemsetAsync(s->ledger, 0, sizeof(DevLedger), s->stream));
+  return refresh_gradient_sites(s);
+}
+
+int cgevap_set_populations(cgevap_sim* s, const void* dev_f, int dtype) {
+  if (!s || !dev_f) return CGEVAP_ERR_ARG;
+  if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
+    return fail(s, CGEVAP_ERR_ARG, "dtype must be F64 or F32");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, launch_set_populations(aux_of(s), dev_f, dtype, s->state[s->cur], s->stream));
+  return refresh_gradient_sites(s);
+}
+
+int cgevap_set_populations_host(cgevap_sim* s, const void* host_f, int dtype) {
+  if (!s || !host_f) return CGEVAP_ERR_ARG;
+  if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
+    return fail(s, CGEVAP_ERR_ARG, "dtype must be F64 or F32");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  const size_t bytes = (size_t)2 * s->Q * s->N * (dtype == CGEVAP_DTYPE_F64 ? 8 : 4);
+  if (s->staging_bytes < bytes) {
+    if (s->staging) cudaFree(s->staging);
+    s->staging = nullptr;
+    s->staging_bytes = 0;
+    if (cudaMalloc(&s->staging, bytes) != cudaSuccess)
+      return fail(s, CGEVAP_ERR_OOM, "cannot allocate staging buffer");
+    s->staging_bytes = bytes;
+  }
+  CG_CUDA(s, cudaMemcpyAsync(s->staging, host_f, bytes, cudaMemcpyHostToDevice, s->stream));
+  int rc = cgevap_set_populations(s, s->staging, dtype);
+  if (rc != CGEVAP_OK) return rc;
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_get_populations(cgevap_sim* s, void* dev_f, int dtype) {
+  if (!s || !dev_f) return CGEVAP_ERR_ARG;
+  if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
+    return fail(s, CGEVAP_ERR_ARG, "dtype must be F64 or F32");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, launch_get_populations(aux_of(s), s->state[s->cur], dev_f, dtype, s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_step(cgevap_sim* s, int nsteps) {
+  if (!s || nsteps < 0) return s ? fail(s, CGEVAP_ERR_ARG, "nsteps < 0") : CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  for (int n = 0; n < nsteps; ++n) {
+    int rc = launch_one_step(s);
+    if (rc != CGEVAP_OK) return rc;
+  }
+  return CGEVAP_OK;
+}
+
+int cgevap_get_macros(cgevap_sim* s, double* rho_r, double* rho_b, double* u, double* rhoN) {
+  if (!s) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, launch_macros(aux_of(s), s->state[s->cur], rho_r, rho_b, u, rhoN, s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_get_mask(cgevap_sim* s, uint8_t* dev_mask) {
+  if (!s || !dev_mask) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, cudaMemcpyAsync(dev_mask, s->mask[s->cur], s->N, cudaMemcpyDeviceToDevice, s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_get_ledger(cgevap_sim* s, cgevap_ledger* out) {
+  if (!s || !out) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  DevLedger d;
+  CG_CUDA(s, cudaMemcpyAsync(&d, s->ledger, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  out->evaporated = d.evaporated;
+  out->last_removed = d.last_removed;
+  out->site_steps = d.site_steps;
+  out->last_sites = d.last_sites;
+  out->steps = d.steps;
+  return CGEVAP_OK;
+}
+
+int cgevap_reset_ledger(cgevap_sim* s) {
+  if (!s) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, cudaMemsetAsync(s->ledger, 0, sizeof(DevLedger), s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_check_health(cgevap_sim* s) {
+  if (!s) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+  CG_CUDA(s, launch_health(aux_of(s), s->state[s->cur], s->flag, s->stream));
+  int h = 0;
+  CG_CUDA(s, cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (h) return fail(s, CGEVAP_ERR_NAN, "non-finite population or non-positive density");
+  return CGEVAP_OK;
+}
+
+// Checkpoint file: magic, version, params, then raw device images (bit-exact restart).
+static const char kMagic[8] = {'C', 'G', 'E', 'V', 'A', 'P', 'C', 'K'};
+static const int kVersion = 1;
+
+int cgevap_save(cgevap_sim* s, const char* path) {
+  if (!s || !path) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  std::vector<char> state(s->state_bytes);
+  std::vector<uint8_t> mask(s->N), solid;
+  std::vector<char> field;
+  DevLedger led;
+  CG_CUDA(s, cudaMemcpyAsync(state.data(), s->state[s->cur], s->state_bytes, cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaMemcpyAsync(mask.data(), s->mask[s->cur], s->N, cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaMemcpyAsync(&led, s->ledger, sizeof(led), cudaMemcpyDeviceToHost, s->stream));
+  const size_t fbytes = s->N * (s->p.storage == CGEVAP_F64 ? 8 : 4);
+  if (s->ph.phi_field) {
+    field.resize(fbytes);
+    CG_CUDA(s, cudaMemcpyAsync(field.data(), s->phi_field, fbytes, cudaMemcpyDeviceToHost, s->stream));
+  }
+  if (s->solid) {
+    solid.resize(s->N);
+    CG_CUDA(s, cudaMemcpyAsync(solid.data(), s->solid, s->N, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(s, CGEVAP_ERR_IO, std::string("cannot open ") + path);
+  const int has_field = field.empty() ? 0 : 1, has_solid = solid.empty() ? 0 : 1;
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&kVersion, sizeof(int), 1, f) == 1 &&
+            std::fwrite(&s->p, sizeof(s->p), 1, f) == 1 &&
+            std::fwrite(&s->phi, sizeof(double), 1, f) == 1 &&
+            std::fwrite(&has_field, sizeof(int), 1, f) == 1 &&
+            std::fwrite(&has_solid, sizeof(int), 1, f) == 1 &&
+            std::fwrite(&led, sizeof(led), 1, f) == 1 &&
+            std::fwrite(state.data(), 1, state.size(), f) == state.size() &&
+            std::fwrite(mask.data(), 1, mask.size(), f) == mask.size() &&
+            (!has_field || std::fwrite(field.data(), 1, field.size(), f) == field.size()) &&
+            (!has_solid || std::fwrite(solid.data(), 1, solid.size(), f) == solid.size());
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(s, CGEVAP_ERR_IO, std::string("write failed: ") + path);
+  return CGEVAP_OK;
+}
+
+int cgevap_load(cgevap_sim* s, const char* path) {
+  if (!s || !path) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(s, CGEVAP_ERR_IO, std::string("cannot open ") + path);
+  char magic[8];
+  int version = 0, has_field = 0, has_solid = 0;
+  cgevap_params p;
+  double phi = 0;
+  DevLedger led;
+  std::vector<char> state(s->state_bytes), field;
+  std::vector<uint8_t> mask(s->N), solid;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+            std::fread(&version, sizeof(int), 1, f) == 1 && version == kVersion &&
+            std::fread(&p, sizeof(p), 1, f) == 1 && std::fread(&phi, sizeof(double), 1, f) == 1 &&
+            std::fread(&has_field, sizeof(int), 1, f) == 1 &&
+            std::fread(&has_solid, sizeof(int), 1, f) == 1 &&
+            std::fread(&led, sizeof(led), 1, f) == 1;
+  if (ok && std::memcmp(&p, &s->p, sizeof(p)) != 0) {
+    std::fclose(f);
+    return fail(s, CGEVAP_ERR_ARG, "checkpoint parameters differ from the handle's");
+  }
+  ok = ok && std::fread(state.data(), 1, state.size(), f) == state.size() &&
+       std::fread(mask.data(), 1, mask.size(), f) == mask.size();
+  const size_t fbytes = s->N * (s->p.storage == CGEVAP_F64 ? 8 : 4);
+  if (ok && has_field) {
+    field.resize(fbytes);
+    ok = std::fread(field.data(), 1, fbytes, f) == fbytes;
+  }
+  if (ok && has_solid) {
+    solid.resize(s->N);
+    ok = std::fread(solid.data(), 1, s->N, f) == (size_t)s->N;
+  }
+  std::fclose(f);
+  if (!ok) return fail(s, CGEVAP_ERR_IO, std::string("malformed checkpoint: ") + path);
+  if (has_solid) {
+    uint8_t* d = nullptr;
+    CG_CUDA(s, cudaMalloc(&d, s->N));
+    cudaError_t e = cudaMemcpy(d, solid.data(), s->N, cudaMemcpyHostToDevice);
+    int rc = e == cudaSuccess ? cgevap_set_solid(s, d) : CGEVAP_ERR_CUDA;
+    cudaStreamSynchronize(s->stream);
+    cudaFree(d);
+    if (rc != CGEVAP_OK) return rc;
+  } else {
+    cgevap_set_solid(s, nullptr);
+  }
+  s->phi = phi;
+  s->ph.varphi = phi / s->p.sbar;
+  if (has_field) {
+    if (!s->phi_field && cudaMalloc(&s->phi_field, fbytes) != cudaSuccess)
+      return fail(s, CGEVAP_ERR_OOM, "cannot allocate flux field");
+    CG_CUDA(s, cudaMemcpyAsync(s->phi_field, field.data(), fbytes, cudaMemcpyHostToDevice, s->stream));
+    s->ph.phi_field = s->phi_field;
+  } else {
+    s->ph.phi_field = nullptr;
+  }
+  CG_CUDA(s, cudaMemcpyAsync(s->state[s->cur], state.data(), s->state_bytes, cudaMemcpyHostToDevice, s->stream));
+  CG_CUDA(s, cudaMemcpyAsync(s->mask[s->cur], mask.data(), s->N, cudaMemcpyHostToDevice, s->stream));
+  CG_CUDA(s, cudaMemcpyAsync(s->ledger, &led, sizeof(led), cudaMemcpyHostToDevice, s->stream));
+  CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CGEVAP_OK;
+}
+
+double cgevap_bytes_per_update(const cgevap_sim* s) {
+  if (!s) return 0.0;
+  const int Q = s->Q;
+  double pops;
+  switch (s->p.storage) {
+    case CGEVAP_F64: pops = 2.0 * 2 * Q * 8; break;
+    case CGEVAP_F32: pops = 2.0 * 2 * Q * 4; break;
+    default: pops = 2.0 * (8 + (Q - 1) * 4); break;
+  }
+  const double mask = s->p.site_rule == CGEVAP_SITES_GRADIENT ? 2.0 : 1.0;
+  const double field = s->ph.phi_field ? (s->p.storage == CGEVAP_F64 ? 8.0 : 4.0) : 0.0;
+  return pops + mask + field;
+}
+
+long long cgevap_fluid_cells(const cgevap_sim* s) { return s ? s->nfluid : 0; }
+
+}  // extern "C"

@@ -1,0 +1,329 @@
+// aux_kernels.cu -- initial equilibrium, population import/export, macroscopic readout, the
+// gradient-rule sites of a given state, solid links and the health check.  One thread per cell;
+// none of these is on the timed path.
+#include "launch.h"
+
+namespace cgevap {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline dim3 grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  if (b < 1) b = 1;
+  return dim3((unsigned)b);
+}
+
+struct Coord {
+  int a, b, m;
+};
+
+__device__ __forceinline__ Coord coord_of(const Geom& g, int cell) {
+  Coord c;
+  c.a = cell % g.na;
+  int t = cell / g.na;
+  c.b = t % g.nb;
+  c.m = t / g.nb;
+  return c;
+}
+
+// Index of (a,b,m) + d, or -1 beyond a wall.
+__device__ __forceinline__ int neighbour(const Geom& g, Coord c, int da, int db, int dm) {
+  int a = step_coord(c.a, da, g.na, g.per_a);
+  int b = step_coord(c.b, db, g.nb, g.per_b);
+  int m = step_coord(c.m, dm, g.nm, g.per_m);
+  if (a < 0 || b < 0 || m < 0) return -1;
+  return (m * g.nb + b) * g.na + a;
+}
+
+__device__ __forceinline__ bool cell_solid(const Geom& g, int cell) {
+  return g.links && (__ldg(g.links + cell) >> 31);
+}
+
+template <int Q, int S>
+__device__ __forceinline__ void store_cell(void* state, const Geom& g, int cell, const double (&fr)[Q],
+                                           const double (&fb)[Q], const Physics& ph) {
+  using R = typename Storage<S>::real;
+  V2<R> f0{(R)fr[0], (R)fb[0]};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) PopIO<S, Q>::store(state, g.ncell, i, cell, (R)fr[i], (R)fb[i], f0, ph);
+}
+
+template <int Q, int S>
+__device__ __forceinline__ void load_cell(const void* state, const Geom& g, int cell, double (&fr)[Q],
+                                          double (&fb)[Q], const Physics& ph) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    auto v = PopIO<S, Q>::load(state, g.ncell, i, i, cell, ph);
+    fr[i] = (double)v.r;
+    fb[i] = (double)v.b;
+  }
+}
+
+__device__ __forceinline__ double read_any(const void* p, int dtype, size_t i) {
+  return dtype == 0 ? reinterpret_cast<const double*>(p)[i] : (double)reinterpret_cast<const float*>(p)[i];
+}
+__device__ __forceinline__ void write_any(void* p, int dtype, size_t i, double v) {
+  if (dtype == 0) reinterpret_cast<double*>(p)[i] = v;
+  else reinterpret_cast<float*>(p)[i] = (float)v;
+}
+
+// f_i^k = rho_k phi_i(alpha_k) + noise (Eq. feq at u = 0).
+template <int Q, int S>
+__global__ void k_init_eq(Geom g, Physics ph, double rri, double rbi, const double* rhoN0,
+                          const void* noise, int ndt, void* state) {
+  using L = Lattice<Q>;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    double fr[Q], fb[Q];
+    const bool solid = cell_solid(g, cell);
+    const double rn = rhoN0[cell];
+    const double rr = rri * (1.0 + rn) / 2.0, rb = rbi * (1.0 - rn) / 2.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (solid) {
+        fr[i] = fb[i] = 0.0;
+        continue;
+      }
+      fr[i] = rr * (L::A(i) + L::B(i) * ph.alpha_r);
+      fb[i] = rb * (L::A(i) + L::B(i) * ph.alpha_b);
+      if (noise) {
+        fr[i] += read_any(noise, ndt, (size_t)i * g.ncell + cell);
+        fb[i] += read_any(noise, ndt, (size_t)(Q + i) * g.ncell + cell);
+      }
+    }
+    store_cell<Q, S>(state, g, cell, fr, fb, ph);
+  }
+}
+
+template <int Q, int S>
+__global__ void k_set_pops(Geom g, Physics ph, const void* in, int dt, void* state) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    double fr[Q], fb[Q];
+    const bool solid = cell_solid(g, cell);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      fr[i] = solid ? 0.0 : read_any(in, dt, (size_t)i * g.ncell + cell);
+      fb[i] = solid ? 0.0 : read_any(in, dt, (size_t)(Q + i) * g.ncell + cell);
+    }
+    store_cell<Q, S>(state, g, cell, fr, fb, ph);
+  }
+}
+
+template <int Q, int S>
+__global__ void k_get_pops(Geom g, Physics ph, const void* state, void* out, int dt) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    double fr[Q], fb[Q];
+    load_cell<Q, S>(state, g, cell, fr, fb, ph);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      write_any(out, dt, (size_t)i * g.ncell + cell, fr[i]);
+      write_any(out, dt, (size_t)(Q + i) * g.ncell + cell, fb[i]);
+    }
+  }
+}
+
+// rho_k, u, rho^N of the state (local sums; Sec. II.A).  u is [3][N] in (x, y, z) order.
+template <int Q, int S>
+__global__ void k_macros(Geom g, Physics ph, const void* state, double* rr_out, double* rb_out,
+                         double* u_out, double* rn_out) {
+  using L = Lattice<Q>;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    double fr[Q], fb[Q];
+    load_cell<Q, S>(state, g, cell, fr, fb, ph);
+    double rr = 0, rb = 0, ja = 0, jb = 0, jm = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rr += fr[i];
+      rb += fb[i];
+      const double f = fr[i] + fb[i];
+      ja += L::ca(i) * f;
+      jb += L::cb(i) * f;
+      jm += L::cm(i) * f;
+    }
+    const double rho = rr + rb;
+    const bool solid = cell_solid(g, cell) || !(rho > 0.0);
+    if (rr_out) rr_out[cell] = solid ? 0.0 : rr;
+    if (rb_out) rb_out[cell] = solid ? 0.0 : rb;
+    if (rn_out) rn_out[cell] = solid ? 0.0 : (rr - rb) / rho;
+    if (u_out) {
+      // (a, b, m) -> (x, y, z): 3D (x, y, z); 2D (x, -, y)
+      const double ux = solid ? 0.0 : ja / rho;
+      const double uy = solid ? 0.0 : (L::D3 ? jb : jm) / rho;
+      const double uz = solid ? 0.0 : (L::D3 ? jm : 0.0) / rho;
+      u_out[cell] = ux;
+      u_out[(size_t)g.ncell + cell] = uy;
+      u_out[2 * (size_t)g.ncell + cell] = uz;
+    }
+  }
+}
+
+// |F| of a state from its local rho^N (Eq. cg): sets bits 1 and 3 of the site byte.
+template <int Q>
+__global__ void k_grad_sites(Geom g, double threshold, const double* rn, uint8_t* mask) {
+  using L = Lattice<Q>;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    if (cell_solid(g, cell)) {
+      mask[cell] = 0;
+      continue;
+    }
+    const Coord c = coord_of(g, cell);
+    const double own = rn[cell];
+    double Fa = 0, Fb = 0, Fm = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      int nb = neighbour(g, c, L::ca(i), L::cb(i), L::cm(i));
+      if (nb >= 0 && cell_solid(g, nb)) nb = -1;
+      const double v = 3.0 * L::W(i) * (nb < 0 ? own : rn[nb]);
+      Fa += L::ca(i) * v;
+      Fb += L::cb(i) * v;
+      Fm += L::cm(i) * v;
+    }
+    const double Fn = sqrt(Fa * Fa + Fb * Fb + Fm * Fm);
+    const double d = Fn - threshold;
+    mask[cell] = (uint8_t)((d > 0 ? 2u : 0u) | (fabs(d) < 1e-6 ? 8u : 0u));
+  }
+}
+
+template <int Q, int S>
+__global__ void k_local_rn(Geom g, Physics ph, const void* state, double* rn) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    double fr[Q], fb[Q];
+    load_cell<Q, S>(state, g, cell, fr, fb, ph);
+    double rr = 0, rb = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rr += fr[i];
+      rb += fb[i];
+    }
+    rn[cell] = (rr + rb > 0.0) ? (rr - rb) / (rr + rb) : 0.0;
+  }
+}
+
+// bit i: pull source x - c_i is solid or beyond a wall; bit 31: the cell is solid.
+template <int Q>
+__global__ void k_links(Geom g, const uint8_t* solid, uint32_t* links) {
+  using L = Lattice<Q>;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    const Coord c = coord_of(g, cell);
+    uint32_t w = solid[cell] ? (1u << 31) : 0u;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int s = neighbour(g, c, -L::ca(i), -L::cb(i), -L::cm(i));
+      if (s < 0 || solid[s]) w |= 1u << i;
+    }
+    links[cell] = w;
+  }
+}
+
+template <int Q, int S>
+__global__ void k_zero_solid(Geom g, Physics ph, void* state) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    if (!cell_solid(g, cell)) continue;
+    double z[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) z[i] = 0.0;
+    store_cell<Q, S>(state, g, cell, z, z, ph);
+  }
+}
+
+template <int Q, int S>
+__global__ void k_health(Geom g, Physics ph, const void* state, int* flag) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    if (cell_solid(g, cell)) continue;
+    double fr[Q], fb[Q];
+    load_cell<Q, S>(state, g, cell, fr, fb, ph);
+    double rho = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bad |= !isfinite(fr[i]) || !isfinite(fb[i]);
+      rho += fr[i] + fb[i];
+    }
+    if (bad || !(rho > 0.0)) atomicOr(flag, 1);
+  }
+}
+
+__global__ void k_convert(const void* in, int in_dt, void* out, int out_double, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    write_any(out, out_double ? 0 : 1, (size_t)i, read_any(in, in_dt, (size_t)i));
+}
+
+}  // namespace
+
+#define CGEVAP_DISPATCH(A, KERNEL, GRID, STREAM, ...)                                            \
+  do {                                                                                            \
+    switch ((A).q * 10 + (A).storage) {                                                           \
+      case 90: KERNEL<9, ST_F64><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;              \
+      case 91: KERNEL<9, ST_F32><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;              \
+      case 92: KERNEL<9, ST_F16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;              \
+      case 93: KERNEL<9, ST_BF16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;             \
+      case 190: KERNEL<19, ST_F64><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
+      case 191: KERNEL<19, ST_F32><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
+      case 192: KERNEL<19, ST_F16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
+      case 193: KERNEL<19, ST_BF16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;           \
+      default: return cudaErrorInvalidValue;                                                      \
+    }                                                                                             \
+  } while (0)
+
+cudaError_t launch_init_equilibrium(const AuxArgs& a, const double* rhoN0, const void* noise,
+                                    int noise_dtype, void* state, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_init_eq, grid_for(a.g.ncell), s, a.g, a.ph, a.rho_r_in, a.rho_b_in, rhoN0,
+                  noise, noise_dtype, state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(const AuxArgs& a, const void* in, int dtype, void* state,
+                                   cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_set_pops, grid_for(a.g.ncell), s, a.g, a.ph, in, dtype, state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(const AuxArgs& a, const void* state, void* out, int dtype,
+                                   cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_get_pops, grid_for(a.g.ncell), s, a.g, a.ph, state, out, dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_macros(const AuxArgs& a, const void* state, double* rho_r, double* rho_b,
+                          double* u, double* rhoN, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_macros, grid_for(a.g.ncell), s, a.g, a.ph, state, rho_r, rho_b, u, rhoN);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_sites(const AuxArgs& a, const void* state, double* tmp_rn,
+                                  uint8_t* mask, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_local_rn, grid_for(a.g.ncell), s, a.g, a.ph, state, tmp_rn);
+  if (a.q == 19)
+    k_grad_sites<19><<<grid_for(a.g.ncell), kThreads, 0, s>>>(a.g, a.ph.threshold, tmp_rn, mask);
+  else
+    k_grad_sites<9><<<grid_for(a.g.ncell), kThreads, 0, s>>>(a.g, a.ph.threshold, tmp_rn, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_links(const AuxArgs& a, const uint8_t* solid, uint32_t* links, cudaStream_t s) {
+  if (a.q == 19)
+    k_links<19><<<grid_for(a.g.ncell), kThreads, 0, s>>>(a.g, solid, links);
+  else
+    k_links<9><<<grid_for(a.g.ncell), kThreads, 0, s>>>(a.g, solid, links);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_solid(const AuxArgs& a, void* state, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_zero_solid, grid_for(a.g.ncell), s, a.g, a.ph, state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_health(const AuxArgs& a, const void* state, int* flag, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_health, grid_for(a.g.ncell), s, a.g, a.ph, state, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
+                                 long long n, cudaStream_t s) {
+  k_convert<<<grid_for(n), kThreads, 0, s>>>(in, in_dtype, out, out_is_double, n);
+  return cudaGetLastError();
+}
+
+}  // namespace cgevap

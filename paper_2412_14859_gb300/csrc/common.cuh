@@ -1,0 +1,133 @@
+// common.cuh -- kernel argument blocks, the device ledger and population load/store helpers.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace cgevap {
+
+// FP64 mass ledger kept on the device (Eq. exchange bookkeeping).
+struct DevLedger {
+  double evaporated;     // cumulative sum of varphi over (site, step) pairs
+  double last_removed;   // sum over the last step's sites
+  long long site_steps;
+  long long last_sites;
+  long long steps;
+};
+
+// Geometry shared by all kernels: sizes along (a, b, m), periodicity, optional solid links.
+struct Geom {
+  int na, nb, nm;          // a = x; b = y (3D) or 1 (2D); m = z (3D) or y (2D)
+  int per_a, per_b, per_m;
+  int ncell;               // na * nb * nm
+  const uint32_t* links;   // per cell: bit i = pull source of direction i is solid or beyond a
+                           // wall, bit 31 = the cell itself is solid; nullptr = no solid cells
+};
+
+struct Physics {
+  double inv_tau_r, inv_tau_b;   // 1 / tau_k
+  double alpha_r, alpha_b;       // Sec. II.A
+  double amp;                    // (9/4) sigma; the perturbation amplitude is amp / tau
+  double beta;                   // Eq. (recolor)
+  int rule;                      // 0 gradient, 1 band
+  double threshold;              // Gamma or theta
+  double varphi;                 // scalar phi / S-bar
+  double inv_sbar;               // 1 / S-bar for a flux field
+  const void* phi_field;         // per-cell phi (double for ST_F64, float otherwise) or nullptr
+  float kap_r[19], kap_b[19];    // deviation storage: phi_i(alpha_k) / phi_0(alpha_k)
+  float scale, inv_scale;        // deviation storage: power-of-two scale of the deviations
+};
+
+struct Reduce {
+  double* part_removed;          // per-block partial sums (scratch, one slot per block)
+  long long* part_sites;
+  unsigned int* done;            // arrival counter, returned to 0 by the last block
+  DevLedger* ledger;
+};
+
+struct StepArgs {
+  Geom g;
+  Physics ph;
+  Reduce red;
+  int ntx, nty;                  // tiles along a and b
+  int pc;                        // planes per chunk along m
+  const void* pin;               // state read (post-recoloring populations of the last step)
+  void* pout;                    // state written
+  const uint8_t* mask_in;        // site bytes of the last step
+  uint8_t* mask_out;             // site bytes of this step
+};
+
+template <class T>
+struct V2 {
+  T r, b;
+};
+
+// ---- population access for each storage format ------------------------------------------------
+
+template <int S, int Q, bool DEV = Storage<S>::dev>
+struct PopIO;
+
+template <int S, int Q>
+struct PopIO<S, Q, false> {
+  using R = typename Storage<S>::real;
+  using Vec = typename Storage<S>::vec;
+  // Population of direction `dir` stored at `cell`, delivered as direction i of the puller.
+  static __device__ __forceinline__ V2<R> load(const void* base, int ncell, int /*i*/, int dir,
+                                               int cell, const Physics&) {
+    const Vec* p = reinterpret_cast<const Vec*>(base) + (size_t)dir * ncell + cell;
+    Vec v = __ldg(p);
+    return {v.x, v.y};
+  }
+  // Stores the populations of one cell; f0 is the rest pair (unused here).
+  static __device__ __forceinline__ void store(void* base, int ncell, int i, int cell, R r, R b,
+                                               V2<R>, const Physics&) {
+    Vec* p = reinterpret_cast<Vec*>(base) + (size_t)i * ncell + cell;
+    Vec v;
+    v.x = r;
+    v.y = b;
+    *p = v;
+  }
+};
+
+template <int S, int Q>
+struct PopIO<S, Q, true> {
+  using R = float;
+  using P = typename Storage<S>::packed;
+  static __device__ __forceinline__ const float2* rest(const void* base) {
+    return reinterpret_cast<const float2*>(base);
+  }
+  // kappa_i = kappa_dir (same speed class), so i selects the constants and dir the address.
+  static __device__ __forceinline__ V2<float> load(const void* base, int ncell, int i, int dir,
+                                                   int cell, const Physics& ph) {
+    float2 f0 = __ldg(rest(base) + cell);
+    if (i == 0) return {f0.x, f0.y};
+    const P* d = reinterpret_cast<const P*>(reinterpret_cast<const char*>(base) +
+                                            dev_block_offset(ncell)) +
+                 (size_t)(dir - 1) * ncell + cell;
+    float2 v = Storage<S>::unpack(__ldg(d));
+    return {fmaf(f0.x, ph.kap_r[i], v.x * ph.inv_scale), fmaf(f0.y, ph.kap_b[i], v.y * ph.inv_scale)};
+  }
+  static __device__ __forceinline__ void store(void* base, int ncell, int i, int cell, float r,
+                                               float b, V2<float> f0, const Physics& ph) {
+    if (i == 0) {
+      reinterpret_cast<float2*>(base)[cell] = make_float2(r, b);
+      return;
+    }
+    P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(base) + dev_block_offset(ncell)) +
+           (size_t)(i - 1) * ncell + cell;
+    *d = Storage<S>::pack((r - f0.r * ph.kap_r[i]) * ph.scale, (b - f0.b * ph.kap_b[i]) * ph.scale);
+  }
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Neighbour coordinate along an axis: v+d wrapped if periodic, -1 beyond a wall.
+__device__ __forceinline__ int step_coord(int v, int d, int n, int per) {
+  int r = v + d;
+  if (r < 0 || r >= n) return per ? wrap(r, n) : -1;
+  return r;
+}
+
+}  // namespace cgevap

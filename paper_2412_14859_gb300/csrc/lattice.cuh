@@ -1,0 +1,164 @@
+// lattice.cuh -- velocity sets, model weights and storage formats of the CUDA path.
+//
+// Coordinates inside the kernels are (a, b, m): a = x (contiguous in memory), b = y for D3Q19
+// (absent for D2Q9), m = the axis the kernels march along (z for D3Q19, y for D2Q9).
+//
+// Weights (paper Sec. II.A defers them to Leclaire et al. 2017; standard values of that model):
+//   W_i  isotropic lattice weights, c_s^2 = 1/3;
+//   A_i + B_i alpha = phi_i(alpha), the rest state of a component with free parameter alpha
+//                     (f_i^eq(rho, 0) = rho phi_i(abar), Eq. feq);
+//   C_i  the constants of the perturbation operator, Eq. (perturb).
+// Opposite directions are adjacent pairs (1,2), (3,4), ..., so opp(i) = i + 1 - 2 ((i-1) & 1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cgevap {
+
+template <int Q>
+struct Lattice;
+
+template <>
+struct Lattice<9> {
+  static constexpr int Q = 9;
+  static constexpr bool D3 = false;
+  // (x, y) of D2Q9 mapped to (a, b, m) = (x, -, y)
+  __host__ __device__ static constexpr int ca(int i) {
+    constexpr int t[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cb(int) { return 0; }
+  __host__ __device__ static constexpr int cm(int i) {
+    constexpr int t[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int speed2(int i) { return i == 0 ? 0 : (i < 5 ? 1 : 2); }
+  __host__ __device__ static constexpr double W(int i) {
+    return speed2(i) == 0 ? 4.0 / 9.0 : (speed2(i) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr double A(int i) {
+    return speed2(i) == 0 ? 0.0 : (speed2(i) == 1 ? 1.0 / 5.0 : 1.0 / 20.0);
+  }
+  __host__ __device__ static constexpr double B(int i) {
+    return speed2(i) == 0 ? 1.0 : (speed2(i) == 1 ? -1.0 / 5.0 : -1.0 / 20.0);
+  }
+  __host__ __device__ static constexpr double C(int i) {
+    return speed2(i) == 0 ? -4.0 / 27.0 : (speed2(i) == 1 ? 2.0 / 27.0 : 5.0 / 108.0);
+  }
+};
+
+template <>
+struct Lattice<19> {
+  static constexpr int Q = 19;
+  static constexpr bool D3 = true;
+  __host__ __device__ static constexpr int ca(int i) {
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cb(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cm(int i) {
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int speed2(int i) { return i == 0 ? 0 : (i < 7 ? 1 : 2); }
+  __host__ __device__ static constexpr double W(int i) {
+    return speed2(i) == 0 ? 1.0 / 3.0 : (speed2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr double A(int i) {
+    return speed2(i) == 0 ? 0.0 : (speed2(i) == 1 ? 1.0 / 12.0 : 1.0 / 24.0);
+  }
+  __host__ __device__ static constexpr double B(int i) {
+    return speed2(i) == 0 ? 1.0 : (speed2(i) == 1 ? -1.0 / 12.0 : -1.0 / 24.0);
+  }
+  __host__ __device__ static constexpr double C(int i) {
+    return speed2(i) == 0 ? -1.0 / 3.0 : (speed2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// 1/|c_i| for the recoloring angle (0 for the rest direction, whose cos is defined as 0).
+template <class L>
+__host__ __device__ constexpr double inv_norm(int i) {
+  return L::speed2(i) == 0 ? 0.0 : (L::speed2(i) == 1 ? 1.0 : 0.70710678118654752440);
+}
+
+// Bit masks of the directions whose pull source x - c_i lies on the low / high side of an axis.
+template <class L>
+__host__ __device__ constexpr uint32_t dirs_where(int axis, int sign) {
+  uint32_t m = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    int c = axis == 0 ? L::ca(i) : (axis == 1 ? L::cb(i) : L::cm(i));
+    if (c == sign) m |= 1u << i;
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------- storage formats ----------
+//
+// ST_F64 / ST_F32: vec2 pops[i][cell] = (f_i^r, f_i^b).  The two components of a direction share
+//   one aligned 16- / 8-byte load, so a pull is Q vector loads per cell.
+// ST_F16 / ST_BF16 ("deviation" storage): float2 rest[cell] = (f_0^r, f_0^b) in FP32 and, for
+//   i >= 1, a packed pair dev[i-1][cell] = s (f_i^k - f_0^k kappa_i^k) in FP16 / BF16, where
+//   kappa_i^k = phi_i(alpha_k) / phi_0(alpha_k) is the ratio of the rest state of component k,
+//   so bulk cells at rest store deviations near 0; s is a power of two (FP16 only) that keeps
+//   small deviations out of the subnormal range.  Decoding multiplies by 1/s exactly.
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+template <int S>
+struct Storage;
+template <>
+struct Storage<ST_F64> {
+  using real = double;
+  using vec = double2;
+  static constexpr bool dev = false;
+  static constexpr int bytes_per_pop = 8;
+};
+template <>
+struct Storage<ST_F32> {
+  using real = float;
+  using vec = float2;
+  static constexpr bool dev = false;
+  static constexpr int bytes_per_pop = 4;
+};
+template <>
+struct Storage<ST_F16> {
+  using real = float;
+  using packed = __half2;
+  static constexpr bool dev = true;
+  static constexpr int bytes_per_pop = 2;
+  static __device__ __forceinline__ float2 unpack(packed p) { return __half22float2(p); }
+  static __device__ __forceinline__ packed pack(float r, float b) { return __floats2half2_rn(r, b); }
+};
+template <>
+struct Storage<ST_BF16> {
+  using real = float;
+  using packed = __nv_bfloat162;
+  static constexpr bool dev = true;
+  static constexpr int bytes_per_pop = 2;
+  static __device__ __forceinline__ float2 unpack(packed p) { return __bfloat1622float2(p); }
+  static __device__ __forceinline__ packed pack(float r, float b) {
+    return __floats2bfloat162_rn(r, b);
+  }
+};
+
+// Byte offset of the deviation block inside one state buffer of a deviation storage.
+__host__ __device__ inline size_t dev_block_offset(long long ncell) {
+  return ((size_t)ncell * sizeof(float2) + 255) & ~(size_t)255;
+}
+
+__host__ inline size_t state_bytes(int storage, int q, long long ncell) {
+  switch (storage) {
+    case ST_F64: return (size_t)q * ncell * sizeof(double2);
+    case ST_F32: return (size_t)q * ncell * sizeof(float2);
+    default: return dev_block_offset(ncell) + (size_t)(q - 1) * ncell * 4;
+  }
+}
+
+}  // namespace cgevap

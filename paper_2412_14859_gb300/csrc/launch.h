@@ -1,0 +1,58 @@
+// launch.h -- host-side launchers of the CUDA kernels (implemented in the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cgevap {
+
+// Tile shapes of the fused step, chosen per lattice by the launch planner / autotuner.
+struct TileCfg {
+  int tx, ty;
+};
+constexpr int kNumTiles3D = 3;
+constexpr TileCfg kTiles3D[kNumTiles3D] = {{32, 8}, {32, 4}, {64, 4}};
+constexpr int kNumTiles2D = 2;
+constexpr TileCfg kTiles2D[kNumTiles2D] = {{128, 1}, {64, 1}};
+
+inline TileCfg tile_cfg(int q, int variant) {
+  return q == 19 ? kTiles3D[variant % kNumTiles3D] : kTiles2D[variant % kNumTiles2D];
+}
+inline int num_tile_variants(int q) { return q == 19 ? kNumTiles3D : kNumTiles2D; }
+
+// Fused step kernels (step_f64.cu, step_f32.cu, step_dev.cu): the __global__ function of a
+// (lattice, storage, tile variant), launched with `threads` threads and one StepArgs argument.
+struct KernelRef {
+  const void* fn;
+  int threads;
+};
+KernelRef step_kernel_f64(int q, int variant);
+KernelRef step_kernel_f32(int q, int variant);
+KernelRef step_kernel_dev(int q, int storage, int variant);
+
+// Auxiliary kernels (aux_kernels.cu).
+struct AuxArgs {
+  Geom g;
+  Physics ph;
+  int q, storage;
+  double rho_r_in, rho_b_in;
+};
+cudaError_t launch_init_equilibrium(const AuxArgs& a, const double* rhoN0, const void* noise,
+                                    int noise_dtype, void* state, cudaStream_t s);
+cudaError_t launch_set_populations(const AuxArgs& a, const void* in, int dtype, void* state,
+                                   cudaStream_t s);
+cudaError_t launch_get_populations(const AuxArgs& a, const void* state, void* out, int dtype,
+                                   cudaStream_t s);
+cudaError_t launch_macros(const AuxArgs& a, const void* state, double* rho_r, double* rho_b,
+                          double* u, double* rhoN, cudaStream_t s);
+cudaError_t launch_gradient_sites(const AuxArgs& a, const void* state, double* tmp_rn,
+                                  uint8_t* mask, cudaStream_t s);
+cudaError_t launch_links(const AuxArgs& a, const uint8_t* solid, uint32_t* links,
+                         cudaStream_t s);
+cudaError_t launch_zero_solid(const AuxArgs& a, void* state, cudaStream_t s);
+cudaError_t launch_health(const AuxArgs& a, const void* state, int* flag, cudaStream_t s);
+cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
+                                 long long n, cudaStream_t s);
+
+}  // namespace cgevap

@@ -1,0 +1,46 @@
+"""Shared helpers of the tests: build the oracle's and the CUDA path's inputs from one seeded
+`inputs.Case`, run both, and compare.  Nothing here computes the method itself."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2412_14859_gb300 import inputs
+
+
+def oracle_params(case: inputs.Case, phi_field=None, solid=None) -> oracle.Params:
+    nz, ny, nx = case.shape
+    return oracle.Params(q=case.q, nx=nx, ny=ny, nz=nz, periodic=tuple(case.periodic),
+                         rho_r_in=case.rho_r_in, rho_b_in=case.rho_b_in, tau_r=case.tau_r,
+                         tau_b=case.tau_b, sigma=case.sigma, beta=case.beta,
+                         site_rule=case.site_rule, threshold=case.threshold, sbar=case.sbar,
+                         phi=case.phi, phi_field=phi_field, solid=solid)
+
+
+def oracle_run(case: inputs.Case, steps: int, phi_field=None, solid=None):
+    p = oracle_params(case, phi_field, solid)
+    run = oracle.Run(p, oracle.init(p, case.phase(), case.noise_array()))
+    run.step(steps)
+    return run
+
+
+def gpu_sim(case: inputs.Case, storage: str, phi_field=None, solid=None):
+    import torch
+    from paper_2412_14859_gb300.binding import Sim
+    sim = Sim.from_case(case, storage)
+    if solid is not None:
+        sim.set_solid(torch.from_numpy(np.ascontiguousarray(solid, np.uint8)).cuda())
+    if phi_field is not None:
+        sim.set_flux(case.phi, torch.from_numpy(np.ascontiguousarray(phi_field)).cuda())
+    else:
+        sim.set_flux(case.phi)
+    rn = torch.from_numpy(case.phase()).cuda()
+    nz = case.noise_array()
+    sim.init_equilibrium(rn, None if nz is None else torch.from_numpy(nz).cuda())
+    return sim
+
+
+def rel_linf(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

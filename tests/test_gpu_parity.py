@@ -1,0 +1,122 @@
+"""Parity of the fused CUDA step (through the C ABI) with the FP64 oracle on the same seeded
+inputs: relative L-infinity of the densities <= 1e-12 for FP64 storage and <= 1e-5 for FP32,
+identical site masks wherever the oracle's decision value lies more than 1e-6 from the
+threshold, and the FP64 ledger equal to the oracle's sum of varphi = phi / S-bar.
+
+Sizes span several tiles of the kernel (32x8 columns in 3D, 128 cells in 2D) plus ragged
+tails, periodic and walled boxes, both site rules, a flux field and interior solids."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_14859_gb300 import inputs
+
+from harness import gpu_sim, oracle_run, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def drop(q, shape, **kw):
+    base = dict(R0=max(3.5, min(s for s in shape if s > 1) / 2.6), noise=1e-6, phi=2e-4, steps=10)
+    base.update(kw)
+    return inputs.Case(f"parity{q}", q, tuple(shape), **base)
+
+
+CASES = [
+    ("2d_periodic_band", drop(9, (1, 40, 300)), 10),
+    ("2d_ragged_gradient", drop(9, (1, 37, 131), site_rule=0, threshold=0.08), 25),
+    ("2d_walls", drop(9, (1, 45, 70), periodic=(0, 0, 1), phi=1e-3), 30),
+    ("2d_density_ratio", drop(9, (1, 48, 64), rho_r_in=4.0, tau_b=0.8, phi=5e-4), 20),
+    ("3d_ragged_band", drop(19, (9, 17, 33)), 10),
+    ("3d_ragged_gradient", drop(19, (11, 21, 37), site_rule=0, threshold=0.08), 12),
+    ("3d_walls_z", drop(19, (14, 20, 40), periodic=(1, 1, 0), phi=1e-3), 15),
+    ("3d_walls_xy", drop(19, (10, 19, 35), periodic=(0, 0, 1), rho_r_in=10.0, tau_b=0.8), 8),
+]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("name,case,steps", CASES, ids=[c[0] for c in CASES])
+def test_step_matches_oracle(name, case, steps, storage):
+    if storage == "f32":
+        # One site decided differently at the threshold moves phi/S-bar of mass; with the
+        # workloads' flux (1e-5) that stays below the FP32 tolerance.
+        case = replace(case, phi=1e-5)
+    run = oracle_run(case, steps)
+    if storage == "f64":
+        # the FP64 comparison is exact only where no decision sat on the threshold
+        assert min(run.min_margin_history) > 1e-9
+    sim = gpu_sim(case, storage)
+    sim.step(steps)
+    g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
+    o = run.macros()
+    tol = TOL[storage]
+    assert rel_linf(g["rho_r"], o["rho_r"]) <= tol
+    assert rel_linf(g["rho_b"], o["rho_b"]) <= tol
+    assert np.max(np.abs(g["u"] - o["u"])) <= tol * 10
+    if storage == "f64":
+        f = sim.populations().cpu().numpy()
+        assert rel_linf(f, run.f) <= tol
+    mask = sim.mask().cpu().numpy()
+    far = run.margin > 1e-6
+    assert np.array_equal(mask[far] & 1, run.mask[far])
+    led = sim.ledger()
+    assert led["steps"] == steps
+    assert led["last_sites"] == run.ledger.last_sites or storage == "f32"
+    assert led["evaporated"] == pytest.approx(run.evaporated, rel=1e-12 if storage == "f64" else 2e-3)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("q,shape", [(9, (1, 36, 150)), (19, (12, 18, 40))])
+def test_flux_field_and_solids(q, shape, storage):
+    scale = 1.0 if storage == "f64" else 1e-2
+    case = drop(q, shape, phi=1e-3 * scale, steps=12)
+    phi = (inputs.uniform_noise(shape, 5e-4, seed=3) + 1e-3) * scale
+    solid = np.zeros(shape, np.uint8)
+    if q == 9:
+        solid[0, 5:9, 20:27] = 1
+        solid[0, 30:, 140:] = 1
+    else:
+        solid[3:6, 2:5, 30:36] = 1
+        solid[:, 15:, :3] = 1
+    run = oracle_run(case, 12, phi_field=phi, solid=solid)
+    if storage == "f64":
+        assert min(run.min_margin_history) > 1e-9
+    sim = gpu_sim(case, storage, phi_field=phi, solid=solid)
+    assert sim.fluid_cells == int((solid == 0).sum())
+    sim.step(12)
+    g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
+    o = run.macros()
+    assert rel_linf(g["rho_r"], o["rho_r"]) <= TOL[storage]
+    assert rel_linf(g["rho_b"], o["rho_b"]) <= TOL[storage]
+    assert np.all(g["rho_r"][solid.astype(bool)] == 0)
+    far = run.margin > 1e-6
+    assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, run.mask[far])
+    assert sim.ledger()["evaporated"] == pytest.approx(
+        run.evaporated, rel=1e-12 if storage == "f64" else 2e-3)
+
+
+@pytest.mark.parametrize("steps", [1, 200])
+def test_long_and_single_step_fp64(steps):
+    case = drop(9, (1, 33, 140), phi=3e-4)
+    run = oracle_run(case, steps)
+    assert min(run.min_margin_history) > 1e-9
+    sim = gpu_sim(case, "f64")
+    sim.step(steps)
+    f = sim.populations().cpu().numpy()
+    assert rel_linf(f, run.f) <= 1e-12
+    assert sim.ledger()["evaporated"] == pytest.approx(run.evaporated, rel=1e-12)
+
+
+def test_gradient_rule_initial_sites_fp64():
+    """Before step 0 the gradient rule uses |F| of the initial state (a reading of Sec. II.B)."""
+    case = drop(19, (8, 16, 34), site_rule=0, threshold=0.1)
+    run = oracle_run(case, 1)
+    sim = gpu_sim(case, "f64")
+    sim.step(1)
+    far = run.margin > 1e-6
+    assert run.mask.sum() > 0
+    assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, run.mask[far])
