@@ -175,6 +175,40 @@ CGEVAP_API double cgevap_bytes_per_update(const cgevap_sim* sim);
 /* Number of fluid cells. */
 CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
 
+/* ---- one timestep without any allocation -------------------------------------------------
+ * No counterpart in the paper; it serves callers that cannot allocate device memory: code running
+ * inside a framework that owns every buffer and forbids allocation in its operators (a custom
+ * call of an XLA/JAX program, an application arena with a fixed budget), which therefore cannot
+ * use cgevap_create.  It advances the state by one step of the same fused kernel as cgevap_step
+ * and calls no cudaMalloc, cudaFree or allocating library routine.  The per-block scratch of the
+ * FP64 ledger fold lives in a static device array of 256 KiB + 256 B, which every GPU that loads
+ * the library holds until the process exits; it fits grids of at most 16384 CTAs (for example
+ * 192^3 D3Q19 needs 288 for FP32).
+ *   p              lattice and physics, validated like cgevap_create (no solids, no flux field);
+ *   phi            scalar flux; each site moves phi / S-bar from red to blue rest populations;
+ *   dev_state_in   caller-owned state in the handle's internal layout (the raw state bytes of a
+ *                  cgevap_save checkpoint): storage F64/F32: Q pairs (f_i^r, f_i^b) per cell as
+ *                  [i][z][y][x] double2/float2; F16DEV/BF16DEV: float2 rest[cell] then, at byte
+ *                  offset round_up(8 N, 256), half2/bfloat162 deviations [i-1][cell];
+ *   dev_state_out  caller-owned buffer of the same size for the new state (not aliasing _in);
+ *   state_bytes    size of each state buffer; must equal that layout's size exactly;
+ *   dev_mask_in    site bytes of the previous step (bits as in cgevap_get_mask), [N];
+ *   dev_mask_out   site bytes written for this step, [N];
+ *   dev_ledger     device cgevap_ledger updated in place (cumulative fields add up);
+ *   cuda_stream    stream to run on (NULL = legacy default stream).
+ * Returns ARG for invalid parameters, NULL or aliasing buffers, a wrong state_bytes, or a lattice
+ * whose grid exceeds 16384 CTAs; CUDA on a failed runtime call; otherwise OK (asynchronous).
+ * The first call on each device resolves the scratch's device address (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture.  Every call on a device
+ * shares the scratch: calls that overlap on the GPU (different streams, concurrent threads) race
+ * and must be serialised by the caller.  The arrival counter in the scratch is cleared on the
+ * stream before each launch; the partial sums need no clearing. */
+CGEVAP_API int cgevap_step_static_scratch(const cgevap_params* p, double phi,
+                                          const void* dev_state_in, void* dev_state_out,
+                                          size_t state_bytes, const uint8_t* dev_mask_in,
+                                          uint8_t* dev_mask_out, cgevap_ledger* dev_ledger,
+                                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,8 @@ _SIGS = {
     "cgevap_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "cgevap_bytes_per_update": (ctypes.c_double, [_vp]),
     "cgevap_fluid_cells": (ctypes.c_longlong, [_vp]),
+    "cgevap_step_static_scratch": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_double, _vp,
+                                                  _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]),
 }
 
 

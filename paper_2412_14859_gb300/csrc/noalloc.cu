@@ -1,0 +1,198 @@
+// noalloc.cu -- cgevap_step_static_scratch: one fused timestep that allocates nothing.
+//
+// The handle API keeps the per-block ledger partials in memory it allocates with cudaMalloc.
+// This entry point is for callers that must not allocate device memory at all -- a framework
+// that owns every buffer and forbids allocation inside its operators (custom calls of an XLA /
+// JAX program, an application arena with a fixed budget), or code that must not call into the
+// allocator at step time.  They pass the state, site bytes and ledger they own; the only scratch
+// the kernel needs lives in the file-scope array below, sized for kMaxBlocks CTAs.
+#include <atomic>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+#include "../../include/cgevap.h"
+#include "launch.h"
+
+using namespace cgevap;
+
+constexpr int kMaxBlocks = 16384;  // largest grid this entry point accepts
+constexpr int kMaxDevices = 64;
+
+// Layout of the scratch: per-block partial sums of the removed mass and the site count, then the
+// arrival counter of the last-block fold.
+constexpr size_t kRemovedOff = 0;
+constexpr size_t kSitesOff = kRemovedOff + sizeof(double) * kMaxBlocks;
+constexpr size_t kDoneOff = kSitesOff + sizeof(long long) * kMaxBlocks;
+constexpr size_t kScratchBytes = kDoneOff + 256;  // 256 KiB + 256 B
+
+// The scratch, shared by every call on a device and kept until the process exits.  In host code
+// `g_scratch` names a host-side stand-in, never the device memory: kernels get the address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+static_assert(sizeof(DevLedger) == sizeof(cgevap_ledger), "ledger layouts must match");
+static_assert(offsetof(cgevap_ledger, steps) == offsetof(DevLedger, steps), "ledger layouts");
+
+namespace {
+
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
+
+// Resolve the device address of g_scratch for the current device (once per device).
+int scratch_on(int device, unsigned char** out) {
+  unsigned char* p = g_scratch_addr[device].load(std::memory_order_acquire);
+  if (!p) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || !addr) return CGEVAP_ERR_CUDA;
+    p = static_cast<unsigned char*>(addr);
+    g_scratch_addr[device].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return CGEVAP_OK;
+}
+
+bool params_ok(const cgevap_params* p) {
+  if (!p) return false;
+  if (p->q != 9 && p->q != 19) return false;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
+  if (p->q == 9 && p->nz != 1) return false;
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return false;
+  for (int d = 0; d < 3; ++d)
+    if (p->periodic[d] != 0 && p->periodic[d] != 1) return false;
+  if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) return false;
+  if (!(p->rho_r_in > 0.0) || !(p->rho_b_in > 0.0)) return false;
+  if (!(p->beta >= 0.0 && p->beta <= 1.0)) return false;
+  if (!(p->sbar > 0.0)) return false;
+  if (!std::isfinite(p->sigma) || !std::isfinite(p->threshold)) return false;
+  if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND) return false;
+  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16DEV) return false;
+  return true;
+}
+
+template <int Q>
+void kappa_of(Physics& ph) {
+  using L = Lattice<Q>;
+  for (int i = 0; i < 19; ++i) {
+    ph.kap_r[i] = ph.kap_b[i] = 0.0f;
+    if (i < Q) {
+      ph.kap_r[i] = (float)((L::A(i) + L::B(i) * ph.alpha_r) / ph.alpha_r);
+      ph.kap_b[i] = (float)((L::A(i) + L::B(i) * ph.alpha_b) / ph.alpha_b);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" CGEVAP_API int cgevap_step_static_scratch(
+    const cgevap_params* p, double phi, const void* dev_state_in, void* dev_state_out,
+    size_t state_bytes_in, const uint8_t* dev_mask_in, uint8_t* dev_mask_out,
+    cgevap_ledger* dev_ledger, void* cuda_stream) {
+  if (!params_ok(p) || !std::isfinite(phi)) return CGEVAP_ERR_ARG;
+  if (!dev_state_in || !dev_state_out || dev_state_in == dev_state_out || !dev_mask_in ||
+      !dev_mask_out || !dev_ledger)
+    return CGEVAP_ERR_ARG;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (state_bytes_in != state_bytes(p->storage, p->q, N)) return CGEVAP_ERR_ARG;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return CGEVAP_ERR_CUDA;
+  if (device < 0 || device >= kMaxDevices) return CGEVAP_ERR_UNSUPPORTED;
+  unsigned char* scratch = nullptr;
+  if (scratch_on(device, &scratch) != CGEVAP_OK) return CGEVAP_ERR_CUDA;
+
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  Geom& g = a.g;
+  g.na = p->nx;
+  if (p->q == 19) {
+    g.nb = p->ny;
+    g.nm = p->nz;
+    g.per_a = p->periodic[0];
+    g.per_b = p->periodic[1];
+    g.per_m = p->periodic[2];
+  } else {
+    g.nb = 1;
+    g.nm = p->ny;
+    g.per_a = p->periodic[0];
+    g.per_b = 1;
+    g.per_m = p->periodic[1];
+  }
+  g.ncell = (int)N;
+  g.links = nullptr;
+
+  Physics& ph = a.ph;
+  const double w0 = p->q == 19 ? Lattice<19>::W(0) : Lattice<9>::W(0);
+  const double rmin = std::fmin(p->rho_r_in, p->rho_b_in);
+  ph.alpha_r = (p->rho_r_in <= rmin) ? w0 : 1.0 - (1.0 - w0) / (p->rho_r_in / rmin);
+  ph.alpha_b = (p->rho_b_in <= rmin) ? w0 : 1.0 - (1.0 - w0) / (p->rho_b_in / rmin);
+  ph.inv_tau_r = 1.0 / p->tau_r;
+  ph.inv_tau_b = 1.0 / p->tau_b;
+  ph.amp = 2.25 * p->sigma;
+  ph.beta = p->beta;
+  ph.rule = p->site_rule;
+  ph.threshold = p->threshold;
+  ph.inv_sbar = 1.0 / p->sbar;
+  ph.varphi = phi / p->sbar;
+  ph.phi_field = nullptr;
+  if (p->q == 19)
+    kappa_of<19>(ph);
+  else
+    kappa_of<9>(ph);
+  if (p->storage == CGEVAP_F16DEV) {
+    const double rmax = std::fmax(p->rho_r_in, p->rho_b_in);
+    int e = (int)std::floor(std::log2(16384.0 / rmax));
+    e = e > 10 ? 10 : (e < 0 ? 0 : e);
+    ph.scale = std::ldexp(1.0f, e);
+  } else {
+    ph.scale = 1.0f;
+  }
+  ph.inv_scale = 1.0f / ph.scale;
+
+  KernelRef k = p->storage == CGEVAP_F64   ? step_kernel_f64(p->q, 0)
+                : p->storage == CGEVAP_F32 ? step_kernel_f32(p->q, 0)
+                                           : step_kernel_dev(p->q, p->storage, 0);
+  if (!k.fn) return CGEVAP_ERR_UNSUPPORTED;
+  int occ = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return CGEVAP_ERR_CUDA;
+  if (occ < 1) occ = 1;
+  const TileCfg t = tile_cfg(p->q, 0);
+  const int ntx = (g.na + t.tx - 1) / t.tx;
+  const int nty = (g.nb + t.ty - 1) / t.ty;
+  const long long tiles = (long long)ntx * nty;
+  const long long slots = (long long)occ * sms;
+  int best_pc = g.nm;
+  double best = 1e300;
+  for (int pc = 1; pc <= g.nm; ++pc) {
+    const long long nchunk = (g.nm + pc - 1) / pc;
+    if (nchunk > 65535 || tiles * nchunk > kMaxBlocks) continue;
+    const double waves = std::ceil((double)(tiles * nchunk) / (double)slots);
+    const double cost = waves * (pc + 2);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_pc = pc;
+    }
+  }
+  const long long nchunk = (g.nm + best_pc - 1) / best_pc;
+  if (tiles * nchunk > kMaxBlocks) return CGEVAP_ERR_ARG;  // lattice too large for the scratch
+
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  unsigned int* done = reinterpret_cast<unsigned int*>(scratch + kDoneOff);
+  if (cudaMemsetAsync(done, 0, sizeof(unsigned int), stream) != cudaSuccess) return CGEVAP_ERR_CUDA;
+  a.red.part_removed = reinterpret_cast<double*>(scratch + kRemovedOff);
+  a.red.part_sites = reinterpret_cast<long long*>(scratch + kSitesOff);
+  a.red.done = done;
+  a.red.ledger = reinterpret_cast<DevLedger*>(dev_ledger);
+  a.ntx = ntx;
+  a.nty = nty;
+  a.pc = best_pc;
+  a.pin = dev_state_in;
+  a.pout = dev_state_out;
+  a.mask_in = dev_mask_in;
+  a.mask_out = dev_mask_out;
+  void* args[] = {&a};
+  if (cudaLaunchKernel(k.fn, dim3((unsigned)tiles, (unsigned)nchunk), dim3(k.threads), args, 0,
+                       stream) != cudaSuccess)
+    return CGEVAP_ERR_CUDA;
+  return CGEVAP_OK;
+}
