@@ -150,7 +150,8 @@ CGEVAP_API int cgevap_get_macros(cgevap_sim* sim, double* dev_rho_r, double* dev
  * within 1e-6 of the threshold, bit3 = gradient rule: | |F| - Gamma | < 1e-6 at that step. */
 CGEVAP_API int cgevap_get_mask(cgevap_sim* sim, uint8_t* dev_mask);
 
-/* Copy the FP64 ledger to the host; synchronises the stream. */
+/* Copy the FP64 ledger to the host; synchronises the stream.  Returns CGEVAP_ERR_TIMEOUT (and
+ * clears the flag) if a bounded device-side wait of a step since the last call gave up. */
 CGEVAP_API int cgevap_get_ledger(cgevap_sim* sim, cgevap_ledger* host_out);
 
 /* Zero the ledger (asynchronous). */
@@ -166,6 +167,16 @@ CGEVAP_API int cgevap_check_health(cgevap_sim* sim);
  * running n + m steps bit for bit.  Both synchronise the stream. Errors: IO, ARG. */
 CGEVAP_API int cgevap_save(cgevap_sim* sim, const char* path);
 CGEVAP_API int cgevap_load(cgevap_sim* sim, const char* path);
+
+/* Select the fused-step kernel: family -1 automatic (the default at create), 0 the
+ * register-pipelined kernel (every storage, any nx), 1 the bulk-copy pipelined kernel (FP32
+ * storage and even nx); variant picks a tile shape / pipeline depth of that family (0 = default);
+ * planes_per_chunk > 0 fixes how many planes one CTA marches through (0 = planner).  All
+ * choices compute the same result; they differ in speed only.  Errors: ARG, UNSUPPORTED. */
+CGEVAP_API int cgevap_tune(cgevap_sim* sim, int family, int variant, int planes_per_chunk);
+/* The current choice of cgevap_tune (any output pointer may be NULL). */
+CGEVAP_API int cgevap_get_tuning(const cgevap_sim* sim, int* family, int* variant,
+                                 int* planes_per_chunk);
 
 /* Bytes the algorithm must move per lattice update of this handle's fused step (populations
  * read and written, site byte read and/or written, flux field read); the numerator of the HBM

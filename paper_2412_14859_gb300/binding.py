@@ -73,6 +73,9 @@ _SIGS = {
     "cgevap_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "cgevap_bytes_per_update": (ctypes.c_double, [_vp]),
     "cgevap_fluid_cells": (ctypes.c_longlong, [_vp]),
+    "cgevap_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cgevap_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cgevap_step_static_scratch": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_double, _vp,
                                                   _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]),
 }
@@ -235,6 +238,16 @@ class Sim:
     def load(self, path: str):
         self._sync_stream()
         self._check(lib().cgevap_load(self._h, path.encode()))
+
+    def tune(self, family: int = -1, variant: int = 0, planes_per_chunk: int = 0):
+        """Pick the fused-step kernel (family -1 auto, 0 register, 1 bulk-copy pipeline)."""
+        self._check(lib().cgevap_tune(self._h, family, variant, planes_per_chunk))
+        return self
+
+    def tuning(self) -> dict:
+        f, v, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().cgevap_get_tuning(self._h, ctypes.byref(f), ctypes.byref(v), ctypes.byref(p)))
+        return {"family": f.value, "variant": v.value, "planes_per_chunk": p.value}
 
     @property
     def bytes_per_update(self) -> float:

@@ -36,9 +36,11 @@ struct cgevap_sim {
   long long part_capacity = 0;
   double* tmp_rn = nullptr;
   int* flag = nullptr;
+  int* status = nullptr;  // set by a bounded device-side wait that gave up
   void* staging = nullptr;  // device staging for host imports
   size_t staging_bytes = 0;
   // launch plan of the fused step
+  int family = 0;  // 0 register-pipelined kernel, 1 bulk-copy pipelined kernel
   int variant = 0;
   KernelRef kernel{nullptr, 0};
   int ntx = 1, nty = 1, pc = 1, nchunk = 1;
@@ -149,14 +151,20 @@ KernelRef kernel_for(int q, int storage, int variant) {
   }
 }
 
+bool bulk_supported(const cgevap_sim* s) {
+  return s->p.storage == CGEVAP_F32 && (s->p.nx % 2) == 0;
+}
+
 // Planes per chunk: balance whole waves of resident CTAs against the two extra planes each
-// chunk pulls (time ~ waves * (pc + 2)).
-int plan_launch(cgevap_sim* s, int variant) {
-  const TileCfg t = tile_cfg(s->p.q, variant);
-  KernelRef k = kernel_for(s->p.q, s->p.storage, variant);
+// chunk pulls (time ~ waves * (pc + 2)); pc_force > 0 overrides.
+int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
+  KernelRef k = family == 1 ? step_bulk_f32(s->p.q, variant)
+                            : kernel_for(s->p.q, s->p.storage, variant);
   if (!k.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
+  TileCfg t = tile_cfg(s->p.q, variant);
+  if (k.tx > 0) t = TileCfg{k.tx, k.ty};
   int occ = 0, sms = 0;
-  CG_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, 0));
+  CG_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, k.smem));
   CG_CUDA(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
   if (occ < 1) occ = 1;
   const int na = s->geom.na, nb = s->geom.nb, nm = s->geom.nm;
@@ -177,6 +185,8 @@ int plan_launch(cgevap_sim* s, int variant) {
       best_pc = pc;
     }
   }
+  if (pc_force > 0) best_pc = pc_force < nm ? pc_force : nm;
+  s->family = family;
   s->variant = variant;
   s->kernel = k;
   s->ntx = ntx;
@@ -208,6 +218,7 @@ int launch_one_step(cgevap_sim* s) {
   a.red.part_sites = s->part_sites;
   a.red.done = s->done;
   a.red.ledger = s->ledger;
+  a.red.status = s->status;
   a.ntx = s->ntx;
   a.nty = s->nty;
   a.pc = s->pc;
@@ -217,7 +228,7 @@ int launch_one_step(cgevap_sim* s) {
   a.mask_out = s->mask[s->cur ^ 1];
   void* args[] = {&a};
   CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
-                              dim3(s->kernel.threads), args, 0, s->stream));
+                              dim3(s->kernel.threads), args, s->kernel.smem, s->stream));
   s->cur ^= 1;
   return CGEVAP_OK;
 }
@@ -237,7 +248,7 @@ void release(cgevap_sim* s) {
   if (!s) return;
   void* ptrs[] = {s->state[0], s->state[1], s->mask[0],  s->mask[1],  s->links,
                   s->solid,    s->phi_field, s->ledger, s->part_removed, s->part_sites,
-                  s->done,     s->tmp_rn,   s->flag,    s->staging};
+                  s->done,     s->tmp_rn,   s->flag,    s->staging, s->status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete s;
@@ -288,7 +299,8 @@ int cgevap_create(const cgevap_params* p, cgevap_sim** out) {
   }
   ok = ok && cudaMalloc(&s->ledger, sizeof(DevLedger)) == cudaSuccess &&
        cudaMalloc(&s->done, sizeof(unsigned int)) == cudaSuccess &&
-       cudaMalloc(&s->flag, sizeof(int)) == cudaSuccess;
+       cudaMalloc(&s->flag, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&s->status, sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     release(s);
@@ -299,12 +311,13 @@ int cgevap_create(const cgevap_params* p, cgevap_sim** out) {
            cudaMemset(s->mask[0], 0, s->N) == cudaSuccess &&
            cudaMemset(s->mask[1], 0, s->N) == cudaSuccess &&
            cudaMemset(s->ledger, 0, sizeof(DevLedger)) == cudaSuccess &&
-           cudaMemset(s->done, 0, sizeof(unsigned int)) == cudaSuccess;
+           cudaMemset(s->done, 0, sizeof(unsigned int)) == cudaSuccess &&
+           cudaMemset(s->status, 0, sizeof(int)) == cudaSuccess;
   if (!z) {
     release(s);
     return fail(nullptr, CGEVAP_ERR_CUDA, "initial memset failed");
   }
-  int rc = plan_launch(s, 0);
+  int rc = plan_launch(s, 0, 0);
   if (rc != CGEVAP_OK) {
     std::string m = s->err;
     release(s);
@@ -471,8 +484,14 @@ int cgevap_get_ledger(cgevap_sim* s, cgevap_ledger* out) {
   if (!s || !out) return CGEVAP_ERR_ARG;
   CG_CUDA(s, cudaSetDevice(s->device));
   DevLedger d;
+  int st = 0;
   CG_CUDA(s, cudaMemcpyAsync(&d, s->ledger, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
+  CG_CUDA(s, cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (st) {
+    cudaMemsetAsync(s->status, 0, sizeof(int), s->stream);
+    return fail(s, CGEVAP_ERR_TIMEOUT, "a device-side wait of the step gave up");
+  }
   out->evaporated = d.evaporated;
   out->last_removed = d.last_removed;
   out->site_steps = d.site_steps;
@@ -602,6 +621,29 @@ int cgevap_load(cgevap_sim* s, const char* path) {
   CG_CUDA(s, cudaMemcpyAsync(s->mask[s->cur], mask.data(), s->N, cudaMemcpyHostToDevice, s->stream));
   CG_CUDA(s, cudaMemcpyAsync(s->ledger, &led, sizeof(led), cudaMemcpyHostToDevice, s->stream));
   CG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CGEVAP_OK;
+}
+
+int cgevap_tune(cgevap_sim* s, int family, int variant, int planes_per_chunk) {
+  if (!s) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  if (family < 0) family = 0;
+  if (family > 1) return fail(s, CGEVAP_ERR_ARG, "kernel family must be -1, 0 or 1");
+  if (family == 1 && !bulk_supported(s))
+    return fail(s, CGEVAP_ERR_UNSUPPORTED, "the bulk-copy kernel needs FP32 storage and an even nx");
+  const int nvar = family == 1 ? (s->p.q == 19 ? kNumBulkVariants3D : kNumBulkVariants2D)
+                               : num_tile_variants(s->p.q);
+  if (variant < 0) variant = 0;
+  if (variant >= nvar) return fail(s, CGEVAP_ERR_ARG, "no such kernel variant");
+  if (planes_per_chunk < 0) return fail(s, CGEVAP_ERR_ARG, "planes_per_chunk < 0");
+  return plan_launch(s, family, variant, planes_per_chunk);
+}
+
+int cgevap_get_tuning(const cgevap_sim* s, int* family, int* variant, int* planes_per_chunk) {
+  if (!s) return CGEVAP_ERR_ARG;
+  if (family) *family = s->family;
+  if (variant) *variant = s->variant;
+  if (planes_per_chunk) *planes_per_chunk = s->pc;
   return CGEVAP_OK;
 }
 

@@ -42,6 +42,7 @@ struct Reduce {
   long long* part_sites;
   unsigned int* done;            // arrival counter, returned to 0 by the last block
   DevLedger* ledger;
+  int* status;                   // set to 1 by a bounded wait that gave up (may be nullptr)
 };
 
 struct StepArgs {

@@ -26,10 +26,16 @@ inline int num_tile_variants(int q) { return q == 19 ? kNumTiles3D : kNumTiles2D
 struct KernelRef {
   const void* fn;
   int threads;
+  int smem = 0;       // dynamic shared memory bytes
+  int tx = 0, ty = 0; // tile shape (0: take it from tile_cfg)
 };
 KernelRef step_kernel_f64(int q, int variant);
 KernelRef step_kernel_f32(int q, int variant);
 KernelRef step_kernel_dev(int q, int storage, int variant);
+// Bulk-copy pipelined step (step_bulk_f32.cu): FP32 storage, nx even.
+constexpr int kNumBulkVariants3D = 2;
+constexpr int kNumBulkVariants2D = 2;
+KernelRef step_bulk_f32(int q, int variant);
 
 // Auxiliary kernels (aux_kernels.cu).
 struct AuxArgs {

@@ -108,28 +108,14 @@ __device__ __forceinline__ typename Storage<S>::real flux_at(const Physics& ph, 
   return (R)__ldg(reinterpret_cast<const R*>(ph.phi_field) + cell) * (R)ph.inv_sbar;
 }
 
-// Pull one cell, decide whether it is a site, apply Eq. (exchange).  Returns rho^N after the
-// exchange; g, rr, rb hold the post-exchange populations and densities.
+// Steps 2-4 for one cell whose pulled populations are in g: decide whether it is a site, apply
+// Eq. (exchange).  Returns rho^N after the exchange; g, rr, rb become post-exchange.
 template <int Q, int S>
-__device__ __forceinline__ typename Storage<S>::real pull_exchange(
-    const StepArgs& A, const Slot& s, const Plane& p, int cell, uint32_t sbits,
-    V2<typename Storage<S>::real> (&g)[Q], typename Storage<S>::real& rr,
-    typename Storage<S>::real& rb, typename Storage<S>::real& e, uint32_t& flags) {
-  using L = Lattice<Q>;
+__device__ __forceinline__ typename Storage<S>::real site_exchange(
+    const StepArgs& A, int cell, V2<typename Storage<S>::real> (&g)[Q],
+    typename Storage<S>::real& rr, typename Storage<S>::real& rb, typename Storage<S>::real& e,
+    uint32_t& flags) {
   using R = typename Storage<S>::real;
-  using IO = PopIO<S, Q>;
-  const Geom& G = A.g;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int ca = L::ca(i), cb = L::cb(i), cm = L::cm(i);
-    const int as = ca > 0 ? s.am1 : (ca < 0 ? s.ap1 : s.a);
-    const int bs = cb > 0 ? s.bm1 : (cb < 0 ? s.bp1 : s.b);
-    const int ms = cm > 0 ? p.mm1 : (cm < 0 ? p.mp1 : p.m);
-    const bool bounce = (sbits >> i) & 1u;
-    const int src = bounce ? cell : (ms * G.nb + bs) * G.na + as;
-    const int dir = bounce ? opp(i) : i;
-    g[i] = IO::load(A.pin, G.ncell, i, dir, src, A.ph);
-  }
   R sr = R(0), sb = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -154,6 +140,30 @@ __device__ __forceinline__ typename Storage<S>::real pull_exchange(
   rb = sb + e;
   flags = (site ? 1u : 0u) | (near ? 4u : 0u);
   return (rr - rb) / (rr + rb);
+}
+
+// Pull one cell (Eq. Stream, pull form; halfway bounce-back where the source is solid), then
+// site_exchange.
+template <int Q, int S>
+__device__ __forceinline__ typename Storage<S>::real pull_exchange(
+    const StepArgs& A, const Slot& s, const Plane& p, int cell, uint32_t sbits,
+    V2<typename Storage<S>::real> (&g)[Q], typename Storage<S>::real& rr,
+    typename Storage<S>::real& rb, typename Storage<S>::real& e, uint32_t& flags) {
+  using L = Lattice<Q>;
+  using IO = PopIO<S, Q>;
+  const Geom& G = A.g;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ca = L::ca(i), cb = L::cb(i), cm = L::cm(i);
+    const int as = ca > 0 ? s.am1 : (ca < 0 ? s.ap1 : s.a);
+    const int bs = cb > 0 ? s.bm1 : (cb < 0 ? s.bp1 : s.b);
+    const int ms = cm > 0 ? p.mm1 : (cm < 0 ? p.mp1 : p.m);
+    const bool bounce = (sbits >> i) & 1u;
+    const int src = bounce ? cell : (ms * G.nb + bs) * G.na + as;
+    const int dir = bounce ? opp(i) : i;
+    g[i] = IO::load(A.pin, G.ncell, i, dir, src, A.ph);
+  }
+  return site_exchange<Q, S>(A, cell, g, rr, rb, e, flags);
 }
 
 template <class R>
