@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--kernel", type=int, default=-1, help="-1 auto, 0 register, 1 TMA pipeline")
+    ap.add_argument("--variant", type=int, default=0, help="tile / pipeline variant of the kernel")
     return ap.parse_args()
 
 
@@ -270,6 +272,8 @@ def run_ours(args, d: Dist):
         K = args.steps
         with torch.cuda.stream(stream):
             sim = Sim.from_case(case, st)
+            if st == "f32":
+                sim.tune(args.kernel, args.variant)
             sim.set_flux(case.phi)
             sim.init_equilibrium(rn, noise)
             sim.step(args.warmup)
@@ -292,7 +296,7 @@ def run_ours(args, d: Dist):
             m = sim.macros()
             rho_r[st] = m["rho_r"]
             led = sim.ledger()
-            results[st] = {"mlups": mlups, "ms": ms_max, "bytes_per_update": bpu,
+            results[st] = {"mlups": mlups, "ms": ms_max, "bytes_per_update": bpu, "tuning": sim.tuning(),
                            "achieved_gbs": achieved, "frac": achieved / hbm, "clocks": clk,
                            "mass_r": float(m["rho_r"].sum()), "ledger": led["evaporated"],
                            "steps_total": led["steps"], "sim": sim}
@@ -328,6 +332,8 @@ def run_ours(args, d: Dist):
             f_host = sim.populations(torch.float32).cpu().pin_memory().numpy()
             sim.close()
             sim2 = Sim.from_case(case, head)
+            if head == "f32":
+                sim2.tune(args.kernel, args.variant)
             sim2.set_flux(case.phi)
             sim2.set_populations_host(f_host)  # allocates the staging buffer once, untimed
             torch.cuda.synchronize()
@@ -367,7 +373,8 @@ def run_ours(args, d: Dist):
                      "traffic": None if traffic is None else round(traffic * cells),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_update": H["bytes_per_update"],
-                     "kernel": "cg_step_kernel (fused step)"},
+                     "kernel": ("cg_step_tma_kernel" if H["tuning"]["family"] == 1 else
+                                "cg_step_kernel") + " (fused step), tuning %s" % H["tuning"]},
         "variants": variants,
         "gpu_launches": args.steps,
     }

@@ -198,11 +198,17 @@ CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
  *   p              lattice and physics, validated like cgevap_create (no solids, no flux field);
  *   phi            scalar flux; each site moves phi / S-bar from red to blue rest populations;
  *   dev_state_in   caller-owned state in the handle's internal layout (the raw state bytes of a
- *                  cgevap_save checkpoint): storage F64/F32: Q pairs (f_i^r, f_i^b) per cell as
- *                  [i][z][y][x] double2/float2; F16DEV/BF16DEV: float2 rest[cell] then, at byte
- *                  offset round_up(8 N, 256), half2/bfloat162 deviations [i-1][cell];
+ *                  cgevap_save checkpoint).  Populations are stored per direction i on a padded
+ *                  grid: pitch P = round_up(nx + 18, 16) elements per row, R = ny + 4 rows per
+ *                  plane (D3Q19; R = 1 for D2Q9), nz planes (ny for D2Q9), so one direction
+ *                  holds E = planes * R * P elements and cell (x, y, z) sits at element
+ *                  (z * R + y + 2) * P + x + 16 (D2Q9: y * P + x + 16); padding and ghost
+ *                  elements are neither read nor written by this entry point.  Storage F64/F32: Q arrays of E pairs
+ *                  (f_i^r, f_i^b) as double2/float2; F16DEV/BF16DEV: E float2 rest pairs, then
+ *                  at byte offset round_up(8 E, 256) Q - 1 arrays of E half2/bfloat162 pairs;
  *   dev_state_out  caller-owned buffer of the same size for the new state (not aliasing _in);
- *   state_bytes    size of each state buffer; must equal that layout's size exactly;
+ *   state_bytes    size of each state buffer; must equal that layout's size exactly
+ *                  (F64: 16 Q E, F32: 8 Q E, 16-bit: round_up(8 E, 256) + 4 (Q - 1) E bytes);
  *   dev_mask_in    site bytes of the previous step (bits as in cgevap_get_mask), [N];
  *   dev_mask_out   site bytes written for this step, [N];
  *   dev_ledger     device cgevap_ledger updated in place (cumulative fields add up);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <cuda.h>
 #include <string>
 #include <vector>
 
@@ -40,9 +41,10 @@ struct cgevap_sim {
   void* staging = nullptr;  // device staging for host imports
   size_t staging_bytes = 0;
   // launch plan of the fused step
-  int family = 0;  // 0 register-pipelined kernel, 1 bulk-copy pipelined kernel
+  int family = 0;  // 0 register-pipelined kernel, 1 TMA-pipelined kernel
   int variant = 0;
   KernelRef kernel{nullptr, 0};
+  alignas(64) unsigned char tmap[2][128];  // TMA tensor maps of state[0] and state[1]
   int ntx = 1, nty = 1, pc = 1, nchunk = 1;
   std::string err;
 };
@@ -151,14 +153,16 @@ KernelRef kernel_for(int q, int storage, int variant) {
   }
 }
 
-bool bulk_supported(const cgevap_sim* s) {
-  return s->p.storage == CGEVAP_F32 && (s->p.nx % 2) == 0;
+bool tma_supported(const cgevap_sim* s) {
+  const Geom& g = s->geom;
+  return s->p.storage == CGEVAP_F32 && (!g.per_a || g.na >= 4) &&
+         (s->p.q == 9 || !g.per_b || g.nb >= 4);
 }
 
 // Planes per chunk: balance whole waves of resident CTAs against the two extra planes each
 // chunk pulls (time ~ waves * (pc + 2)); pc_force > 0 overrides.
 int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
-  KernelRef k = family == 1 ? step_bulk_f32(s->p.q, variant)
+  KernelRef k = family == 1 ? step_tma_f32(s->p.q, variant)
                             : kernel_for(s->p.q, s->p.storage, variant);
   if (!k.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
   TileCfg t = tile_cfg(s->p.q, variant);
@@ -186,6 +190,20 @@ int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
     }
   }
   if (pc_force > 0) best_pc = pc_force < nm ? pc_force : nm;
+  if (k.needs_map) {
+    const int bh = s->p.q == 19 ? t.ty + 2 : 1;
+    for (int h = 0; h < 2; ++h) {
+      int rc = make_pop_tensor_map(s->tmap[h], s->state[h], s->geom, s->p.q, 8, t.tx + 4, bh);
+      if (rc != 0) return fail(s, CGEVAP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(rc));
+    }
+  }
+  // the TMA kernel reads periodic images from the ghost layers: keep them from now on
+  const int want_a = family == 1 && s->geom.per_a && s->geom.na >= 4;
+  const int want_b = family == 1 && s->p.q == 19 && s->geom.per_b && s->geom.nb >= 4;
+  const bool turn_on = (want_a && !s->geom.img_a) || (want_b && !s->geom.img_b);
+  s->geom.img_a = want_a;
+  s->geom.img_b = want_b;
+  if (turn_on) CG_CUDA(s, launch_fill_ghosts(aux_of(s), s->state[s->cur], s->stream));
   s->family = family;
   s->variant = variant;
   s->kernel = k;
@@ -226,7 +244,7 @@ int launch_one_step(cgevap_sim* s) {
   a.pout = s->state[s->cur ^ 1];
   a.mask_in = s->mask[s->cur];
   a.mask_out = s->mask[s->cur ^ 1];
-  void* args[] = {&a};
+  void* args[] = {&a, s->tmap[s->cur]};
   CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
                               dim3(s->kernel.threads), args, s->kernel.smem, s->stream));
   s->cur ^= 1;
@@ -290,8 +308,19 @@ int cgevap_create(const cgevap_params* p, cgevap_sim** out) {
   }
   g.ncell = (int)s->N;
   g.links = nullptr;
+  const StoreShape sh = store_shape(p->q, p->nx, p->ny, p->nz);
+  if ((long long)p->q * sh.nstore >= (1LL << 31)) {
+    release(s);
+    return fail(nullptr, CGEVAP_ERR_ARG, "lattice too large for 32-bit storage indices");
+  }
+  g.gy = p->q == 19 ? 2 : 0;
+  g.pitch = sh.pitch;
+  g.rows = sh.rows;
+  g.nstore = (int)sh.nstore;
+  g.img_a = 0;  // ghost images are kept only while the TMA kernel is selected
+  g.img_b = 0;
   setup_physics(s);
-  s->state_bytes = state_bytes(p->storage, p->q, s->N);
+  s->state_bytes = state_bytes(p->storage, p->q, sh.nstore);
   bool ok = true;
   for (int h = 0; h < 2 && ok; ++h) {
     ok = cudaMalloc(&s->state[h], s->state_bytes) == cudaSuccess &&
@@ -627,11 +656,12 @@ int cgevap_load(cgevap_sim* s, const char* path) {
 int cgevap_tune(cgevap_sim* s, int family, int variant, int planes_per_chunk) {
   if (!s) return CGEVAP_ERR_ARG;
   CG_CUDA(s, cudaSetDevice(s->device));
-  if (family < 0) family = 0;
+  if (family < 0) family = tma_supported(s) ? 1 : 0;
   if (family > 1) return fail(s, CGEVAP_ERR_ARG, "kernel family must be -1, 0 or 1");
-  if (family == 1 && !bulk_supported(s))
-    return fail(s, CGEVAP_ERR_UNSUPPORTED, "the bulk-copy kernel needs FP32 storage and an even nx");
-  const int nvar = family == 1 ? (s->p.q == 19 ? kNumBulkVariants3D : kNumBulkVariants2D)
+  if (family == 1 && !tma_supported(s))
+    return fail(s, CGEVAP_ERR_UNSUPPORTED,
+                "the TMA kernel needs FP32 storage and >= 4 cells along periodic x and y");
+  const int nvar = family == 1 ? (s->p.q == 19 ? kNumTmaVariants3D : kNumTmaVariants2D)
                                : num_tile_variants(s->p.q);
   if (variant < 0) variant = 0;
   if (variant >= nvar) return fail(s, CGEVAP_ERR_ARG, "no such kernel variant");

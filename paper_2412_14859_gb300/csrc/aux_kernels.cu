@@ -42,21 +42,28 @@ __device__ __forceinline__ bool cell_solid(const Geom& g, int cell) {
   return g.links && (__ldg(g.links + cell) >> 31);
 }
 
+// Stores the populations of a cell (compact index) at its storage index and periodic images.
 template <int Q, int S>
 __device__ __forceinline__ void store_cell(void* state, const Geom& g, int cell, const double (&fr)[Q],
                                            const double (&fb)[Q], const Physics& ph) {
   using R = typename Storage<S>::real;
+  const Coord c = coord_of(g, cell);
+  const Images im = images_of(g, c.a, c.b, c.m);
   V2<R> f0{(R)fr[0], (R)fb[0]};
 #pragma unroll
-  for (int i = 0; i < Q; ++i) PopIO<S, Q>::store(state, g.ncell, i, cell, (R)fr[i], (R)fb[i], f0, ph);
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < im.n; ++j)
+      PopIO<S, Q>::store(state, g.nstore, i, im.s[j], (R)fr[i], (R)fb[i], f0, ph);
 }
 
 template <int Q, int S>
 __device__ __forceinline__ void load_cell(const void* state, const Geom& g, int cell, double (&fr)[Q],
                                           double (&fb)[Q], const Physics& ph) {
+  const Coord c = coord_of(g, cell);
+  const int si = sidx(g, c.a, c.b, c.m);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    auto v = PopIO<S, Q>::load(state, g.ncell, i, i, cell, ph);
+    auto v = PopIO<S, Q>::load(state, g.nstore, i, i, si, ph);
     fr[i] = (double)v.r;
     fb[i] = (double)v.b;
   }
@@ -245,6 +252,30 @@ __global__ void k_health(Geom g, Physics ph, const void* state, int* flag) {
   }
 }
 
+// Copy every cell within two of a periodic x / y edge into its ghost images (raw storage bits).
+template <int Q, int S>
+__global__ void k_fill_ghosts(Geom g, void* state) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += gridDim.x * blockDim.x) {
+    const Coord c = coord_of(g, cell);
+    const Images im = images_of(g, c.a, c.b, c.m);
+    if (im.n < 2) continue;
+    if (Storage<S>::dev) {
+      float2* rest = reinterpret_cast<float2*>(state);
+      uint32_t* dev = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(state) + dev_block_offset(g.nstore));
+      for (int j = 1; j < im.n; ++j) {
+        rest[im.s[j]] = rest[im.s[0]];
+        for (int i = 1; i < Q; ++i)
+          dev[(size_t)(i - 1) * g.nstore + im.s[j]] = dev[(size_t)(i - 1) * g.nstore + im.s[0]];
+      }
+    } else {
+      using Vec = typename Storage<(S == ST_F64 ? ST_F64 : ST_F32)>::vec;
+      Vec* p = reinterpret_cast<Vec*>(state);
+      for (int j = 1; j < im.n; ++j)
+        for (int i = 0; i < Q; ++i) p[(size_t)i * g.nstore + im.s[j]] = p[(size_t)i * g.nstore + im.s[0]];
+    }
+  }
+}
+
 __global__ void k_convert(const void* in, int in_dt, void* out, int out_double, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     write_any(out, out_double ? 0 : 1, (size_t)i, read_any(in, in_dt, (size_t)i));
@@ -317,6 +348,11 @@ cudaError_t launch_zero_solid(const AuxArgs& a, void* state, cudaStream_t s) {
 
 cudaError_t launch_health(const AuxArgs& a, const void* state, int* flag, cudaStream_t s) {
   CGEVAP_DISPATCH(a, k_health, grid_for(a.g.ncell), s, a.g, a.ph, state, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_fill_ghosts, grid_for(a.g.ncell), s, a.g, state);
   return cudaGetLastError();
 }
 

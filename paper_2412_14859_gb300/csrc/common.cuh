@@ -15,13 +15,51 @@ struct DevLedger {
 };
 
 // Geometry shared by all kernels: sizes along (a, b, m), periodicity, optional solid links.
+//
+// Per-cell fields (site bytes, links, flux) use the compact index cell = (m*nb + b)*na + a.
+// Population arrays use the padded storage index sidx(a, b, m): each stored row holds `pitch`
+// elements, a = 0 sits at element kOx of its row (x = 0 of FP32 pairs on a 128-byte line) with
+// two ghost columns before it and two after a = na-1, and in 3D each plane holds `rows` rows
+// with two ghost rows before b = 0 and after b = nb-1.  While img_a / img_b are set (the TMA
+// kernel is selected), the ghosts along that periodic axis hold the periodic images of the two
+// nearest cells on the other side, written by every kernel that writes populations, so a box of
+// the tile plus two cells never has to wrap.
 struct Geom {
   int na, nb, nm;          // a = x; b = y (3D) or 1 (2D); m = z (3D) or y (2D)
   int per_a, per_b, per_m;
   int ncell;               // na * nb * nm
   const uint32_t* links;   // per cell: bit i = pull source of direction i is solid or beyond a
                            // wall, bit 31 = the cell itself is solid; nullptr = no solid cells
+  int gy;                  // ghost rows on each side of b: 2 in 3D, 0 in 2D (ghost columns: 2)
+  int pitch;               // stored elements per row: round_up(na + kOx + 2, 16)
+  int rows;                // stored rows per plane: nb + 2 gy
+  int nstore;              // stored elements per population array: nm * rows * pitch
+  int img_a, img_b;        // 1 where the periodic images along a / b are maintained
 };
+
+__host__ __device__ __forceinline__ int sidx(const Geom& g, int a, int b, int m) {
+  return (m * g.rows + b + g.gy) * g.pitch + a + kOx;
+}
+
+// Storage indices of a cell and of its periodic ghost images (1 to 4 entries).
+struct Images {
+  int n;
+  int s[4];
+};
+
+__device__ __forceinline__ Images images_of(const Geom& g, int a, int b, int m) {
+  Images im;
+  const int base = sidx(g, a, b, m);
+  int da = 0, db = 0;
+  if (g.img_a) da = a < 2 ? g.na : (a >= g.na - 2 ? -g.na : 0);
+  if (g.img_b) db = b < 2 ? g.nb : (b >= g.nb - 2 ? -g.nb : 0);
+  im.n = 1;
+  im.s[0] = base;
+  if (da) im.s[im.n++] = base + da;
+  if (db) im.s[im.n++] = base + db * g.pitch;
+  if (da && db) im.s[im.n++] = base + da + db * g.pitch;
+  return im;
+}
 
 struct Physics {
   double inv_tau_r, inv_tau_b;   // 1 / tau_k
@@ -71,17 +109,17 @@ template <int S, int Q>
 struct PopIO<S, Q, false> {
   using R = typename Storage<S>::real;
   using Vec = typename Storage<S>::vec;
-  // Population of direction `dir` stored at `cell`, delivered as direction i of the puller.
-  static __device__ __forceinline__ V2<R> load(const void* base, int ncell, int /*i*/, int dir,
-                                               int cell, const Physics&) {
-    const Vec* p = reinterpret_cast<const Vec*>(base) + (size_t)dir * ncell + cell;
+  // Population of direction `dir` stored at storage index `si`, delivered as direction i.
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int /*i*/, int dir,
+                                               int si, const Physics&) {
+    const Vec* p = reinterpret_cast<const Vec*>(base) + (size_t)dir * nstore + si;
     Vec v = __ldg(p);
     return {v.x, v.y};
   }
-  // Stores the populations of one cell; f0 is the rest pair (unused here).
-  static __device__ __forceinline__ void store(void* base, int ncell, int i, int cell, R r, R b,
+  // Stores one population pair at storage index si; f0 is the rest pair (unused here).
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
                                                V2<R>, const Physics&) {
-    Vec* p = reinterpret_cast<Vec*>(base) + (size_t)i * ncell + cell;
+    Vec* p = reinterpret_cast<Vec*>(base) + (size_t)i * nstore + si;
     Vec v;
     v.x = r;
     v.y = b;
@@ -97,24 +135,24 @@ struct PopIO<S, Q, true> {
     return reinterpret_cast<const float2*>(base);
   }
   // kappa_i = kappa_dir (same speed class), so i selects the constants and dir the address.
-  static __device__ __forceinline__ V2<float> load(const void* base, int ncell, int i, int dir,
-                                                   int cell, const Physics& ph) {
-    float2 f0 = __ldg(rest(base) + cell);
+  static __device__ __forceinline__ V2<float> load(const void* base, int nstore, int i, int dir,
+                                                   int si, const Physics& ph) {
+    float2 f0 = __ldg(rest(base) + si);
     if (i == 0) return {f0.x, f0.y};
     const P* d = reinterpret_cast<const P*>(reinterpret_cast<const char*>(base) +
-                                            dev_block_offset(ncell)) +
-                 (size_t)(dir - 1) * ncell + cell;
+                                            dev_block_offset(nstore)) +
+                 (size_t)(dir - 1) * nstore + si;
     float2 v = Storage<S>::unpack(__ldg(d));
     return {fmaf(f0.x, ph.kap_r[i], v.x * ph.inv_scale), fmaf(f0.y, ph.kap_b[i], v.y * ph.inv_scale)};
   }
-  static __device__ __forceinline__ void store(void* base, int ncell, int i, int cell, float r,
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, float r,
                                                float b, V2<float> f0, const Physics& ph) {
     if (i == 0) {
-      reinterpret_cast<float2*>(base)[cell] = make_float2(r, b);
+      reinterpret_cast<float2*>(base)[si] = make_float2(r, b);
       return;
     }
-    P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(base) + dev_block_offset(ncell)) +
-           (size_t)(i - 1) * ncell + cell;
+    P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(base) + dev_block_offset(nstore)) +
+           (size_t)(i - 1) * nstore + si;
     *d = Storage<S>::pack((r - f0.r * ph.kap_r[i]) * ph.scale, (b - f0.b * ph.kap_b[i]) * ph.scale);
   }
 };

@@ -149,15 +149,32 @@ struct Storage<ST_BF16> {
 };
 
 // Byte offset of the deviation block inside one state buffer of a deviation storage.
-__host__ __device__ inline size_t dev_block_offset(long long ncell) {
-  return ((size_t)ncell * sizeof(float2) + 255) & ~(size_t)255;
+__host__ __device__ inline size_t dev_block_offset(long long nstore) {
+  return ((size_t)nstore * sizeof(float2) + 255) & ~(size_t)255;
 }
 
-__host__ inline size_t state_bytes(int storage, int q, long long ncell) {
+// Padded storage of a lattice (see Geom in common.cuh): pitch, rows per plane, elements per
+// population array.  kOx = stored elements before x = 0 in each row (the last two are ghosts);
+// 16 puts x = 0 of FP32 / rest pairs on a 128-byte line boundary.
+constexpr int kOx = 16;
+struct StoreShape {
+  int pitch, rows;
+  long long nstore;
+};
+__host__ inline StoreShape store_shape(int q, int nx, int ny, int nz) {
+  StoreShape s;
+  s.pitch = (nx + kOx + 2 + 15) & ~15;
+  s.rows = q == 19 ? ny + 4 : 1;
+  const long long planes = q == 19 ? nz : ny;
+  s.nstore = planes * s.rows * (long long)s.pitch;
+  return s;
+}
+
+__host__ inline size_t state_bytes(int storage, int q, long long nstore) {
   switch (storage) {
-    case ST_F64: return (size_t)q * ncell * sizeof(double2);
-    case ST_F32: return (size_t)q * ncell * sizeof(float2);
-    default: return dev_block_offset(ncell) + (size_t)(q - 1) * ncell * 4;
+    case ST_F64: return (size_t)q * nstore * sizeof(double2);
+    case ST_F32: return (size_t)q * nstore * sizeof(float2);
+    default: return dev_block_offset(nstore) + (size_t)(q - 1) * nstore * 4;
   }
 }
 

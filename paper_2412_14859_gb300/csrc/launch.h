@@ -12,7 +12,7 @@ struct TileCfg {
   int tx, ty;
 };
 constexpr int kNumTiles3D = 3;
-constexpr TileCfg kTiles3D[kNumTiles3D] = {{32, 8}, {32, 4}, {64, 4}};
+constexpr TileCfg kTiles3D[kNumTiles3D] = {{32, 8}, {32, 16}, {32, 16}};
 constexpr int kNumTiles2D = 2;
 constexpr TileCfg kTiles2D[kNumTiles2D] = {{128, 1}, {64, 1}};
 
@@ -28,14 +28,19 @@ struct KernelRef {
   int threads;
   int smem = 0;       // dynamic shared memory bytes
   int tx = 0, ty = 0; // tile shape (0: take it from tile_cfg)
+  int needs_map = 0;  // 1: second kernel argument is the TMA tensor map of the input state
 };
 KernelRef step_kernel_f64(int q, int variant);
 KernelRef step_kernel_f32(int q, int variant);
 KernelRef step_kernel_dev(int q, int storage, int variant);
-// Bulk-copy pipelined step (step_bulk_f32.cu): FP32 storage, nx even.
-constexpr int kNumBulkVariants3D = 2;
-constexpr int kNumBulkVariants2D = 2;
-KernelRef step_bulk_f32(int q, int variant);
+// TMA-pipelined step (step_tma_f32.cu): FP32 storage; periodic axes need >= 4 cells.
+constexpr int kNumTmaVariants3D = 2;
+constexpr int kNumTmaVariants2D = 2;
+KernelRef step_tma_f32(int q, int variant);
+// TMA tensor map (128-byte CUtensorMap written to `map`) of one population buffer: elements of
+// elem_bytes, box of box_w x box_h (x, rows) per direction and plane.  Returns 0 on success.
+int make_pop_tensor_map(void* map, const void* base, const Geom& g, int q, int elem_bytes,
+                        int box_w, int box_h);
 
 // Auxiliary kernels (aux_kernels.cu).
 struct AuxArgs {
@@ -58,6 +63,7 @@ cudaError_t launch_links(const AuxArgs& a, const uint8_t* solid, uint32_t* links
                          cudaStream_t s);
 cudaError_t launch_zero_solid(const AuxArgs& a, void* state, cudaStream_t s);
 cudaError_t launch_health(const AuxArgs& a, const void* state, int* flag, cudaStream_t s);
+cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s);
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s);
 

@@ -92,7 +92,9 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
       !dev_mask_out || !dev_ledger)
     return CGEVAP_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (state_bytes_in != state_bytes(p->storage, p->q, N)) return CGEVAP_ERR_ARG;
+  const StoreShape sh = store_shape(p->q, p->nx, p->ny, p->nz);
+  if ((long long)p->q * sh.nstore >= (1LL << 31)) return CGEVAP_ERR_ARG;
+  if (state_bytes_in != state_bytes(p->storage, p->q, sh.nstore)) return CGEVAP_ERR_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return CGEVAP_ERR_CUDA;
   if (device < 0 || device >= kMaxDevices) return CGEVAP_ERR_UNSUPPORTED;
@@ -118,6 +120,12 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
   }
   g.ncell = (int)N;
   g.links = nullptr;
+  g.gy = p->q == 19 ? 2 : 0;
+  g.pitch = sh.pitch;
+  g.rows = sh.rows;
+  g.nstore = (int)sh.nstore;
+  g.img_a = 0;  // the register kernel keeps no ghost images
+  g.img_b = 0;
 
   Physics& ph = a.ph;
   const double w0 = p->q == 19 ? Lattice<19>::W(0) : Lattice<9>::W(0);
@@ -152,11 +160,12 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
                                            : step_kernel_dev(p->q, p->storage, 0);
   if (!k.fn) return CGEVAP_ERR_UNSUPPORTED;
   int occ = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, k.smem) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return CGEVAP_ERR_CUDA;
   if (occ < 1) occ = 1;
-  const TileCfg t = tile_cfg(p->q, 0);
+  TileCfg t = tile_cfg(p->q, 0);
+  if (k.tx > 0) t = TileCfg{k.tx, k.ty};
   const int ntx = (g.na + t.tx - 1) / t.tx;
   const int nty = (g.nb + t.ty - 1) / t.ty;
   const long long tiles = (long long)ntx * nty;
@@ -191,8 +200,8 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
   a.mask_in = dev_mask_in;
   a.mask_out = dev_mask_out;
   void* args[] = {&a};
-  if (cudaLaunchKernel(k.fn, dim3((unsigned)tiles, (unsigned)nchunk), dim3(k.threads), args, 0,
-                       stream) != cudaSuccess)
+  if (cudaLaunchKernel(k.fn, dim3((unsigned)tiles, (unsigned)nchunk), dim3(k.threads), args,
+                       k.smem, stream) != cudaSuccess)
     return CGEVAP_ERR_CUDA;
   return CGEVAP_OK;
 }

@@ -4,17 +4,34 @@
 
 namespace cgevap {
 
+template <int Q, int TX, int TY, int MINB, int CPT>
+static KernelRef reg_ref() {
+  constexpr int smem = CPT * Q * TX * TY * 8;
+  const void* fn = (const void*)cg_step_kernel<Q, ST_F32, TX, TY, MINB, CPT>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return {nullptr, 0};
+    attr = true;
+  }
+  KernelRef k{fn, TX * TY};
+  k.smem = smem;
+  k.tx = TX;
+  k.ty = TY * CPT;
+  return k;
+}
+
 KernelRef step_kernel_f32(int q, int variant) {
   if (q == 19) {
     switch (variant) {
-      case 0: return {(const void*)cg_step_kernel<19, ST_F32, 32, 8, 2>, 256};
-      case 1: return {(const void*)cg_step_kernel<19, ST_F32, 32, 4, 4>, 128};
-      case 2: return {(const void*)cg_step_kernel<19, ST_F32, 64, 4, 2>, 256};
+      case 0: return reg_ref<19, 32, 8, 2, 1>();
+      case 1: return reg_ref<19, 32, 8, 2, 2>();
+      case 2: return reg_ref<19, 32, 16, 1, 1>();
     }
   } else if (q == 9) {
     switch (variant) {
-      case 0: return {(const void*)cg_step_kernel<9, ST_F32, 128, 1, 4>, 128};
-      case 1: return {(const void*)cg_step_kernel<9, ST_F32, 64, 1, 8>, 64};
+      case 0: return reg_ref<9, 128, 1, 4, 1>();
+      case 1: return reg_ref<9, 64, 1, 8, 1>();
     }
   }
   return {nullptr, 0};

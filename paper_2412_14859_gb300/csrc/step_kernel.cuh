@@ -15,6 +15,8 @@
 // into the device ledger (deterministic).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cgevap {
@@ -22,6 +24,7 @@ namespace cgevap {
 struct Slot {
   int a, b;                // wrapped coordinates
   int am1, ap1, bm1, bp1;  // neighbours along a and b (-1 beyond a wall)
+  int dxm, dxp, dym, dyp;  // storage offsets to the pull sources at a-1, a+1, b-1, b+1
   bool ok;                 // false beyond a wall
 };
 
@@ -48,6 +51,11 @@ __device__ __forceinline__ Slot make_slot(const Geom& g, int ua, int ub) {
   s.ap1 = step_coord(a, +1, g.na, g.per_a);
   s.bm1 = L::D3 ? step_coord(b, -1, g.nb, g.per_b) : 0;
   s.bp1 = L::D3 ? step_coord(b, +1, g.nb, g.per_b) : 0;
+  // beyond a wall the offset is never used (the link bounces back); keep it in bounds anyway
+  s.dxm = s.am1 >= 0 ? s.am1 - a : 0;
+  s.dxp = s.ap1 >= 0 ? s.ap1 - a : 0;
+  s.dym = s.bm1 >= 0 ? (s.bm1 - b) * g.pitch : 0;
+  s.dyp = s.bp1 >= 0 ? (s.bp1 - b) * g.pitch : 0;
   return s;
 }
 
@@ -108,13 +116,25 @@ __device__ __forceinline__ typename Storage<S>::real flux_at(const Physics& ph, 
   return (R)__ldg(reinterpret_cast<const R*>(ph.phi_field) + cell) * (R)ph.inv_sbar;
 }
 
+template <class R>
+__device__ __forceinline__ R recip(R x);
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return 1.0 / x;
+}
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  return __frcp_rn(x);
+}
+
 // Steps 2-4 for one cell whose pulled populations are in g: decide whether it is a site, apply
-// Eq. (exchange).  Returns rho^N after the exchange; g, rr, rb become post-exchange.
+// Eq. (exchange).  Returns rho^N after the exchange; g, rr, rb become post-exchange and irho is
+// 1 / rho (rho is not changed by the exchange).
 template <int Q, int S>
 __device__ __forceinline__ typename Storage<S>::real site_exchange(
     const StepArgs& A, int cell, V2<typename Storage<S>::real> (&g)[Q],
     typename Storage<S>::real& rr, typename Storage<S>::real& rb, typename Storage<S>::real& e,
-    uint32_t& flags) {
+    uint32_t& flags, typename Storage<S>::real& irho) {
   using R = typename Storage<S>::real;
   R sr = R(0), sb = R(0);
 #pragma unroll
@@ -122,10 +142,11 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
     sr += g[i].r;
     sb += g[i].b;
   }
+  irho = recip<R>(sr + sb);
+  const R rn_pre = (sr - sb) * irho;
   bool site, near;
   if (A.ph.rule == 1) {
-    const R rn = (sr - sb) / (sr + sb);
-    const R d = fabs(rn) - (R)A.ph.threshold;
+    const R d = fabs(rn_pre) - (R)A.ph.threshold;
     site = d < R(0);
     near = fabs(d) < R(1e-6);
   } else {
@@ -139,31 +160,45 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
   rr = sr - e;
   rb = sb + e;
   flags = (site ? 1u : 0u) | (near ? 4u : 0u);
-  return (rr - rb) / (rr + rb);
+  return rn_pre - R(2) * e * irho;
 }
 
-// Pull one cell (Eq. Stream, pull form; halfway bounce-back where the source is solid), then
-// site_exchange.
+// Storage offsets from a cell in plane m to its pull sources in planes m-1 (dm_lo, used by
+// directions with c_m = +1) and m+1 (dm_hi); 0 where that plane lies beyond a wall (those links
+// bounce back and the offset is never used).
+struct PlaneOffsets {
+  int dm_lo, dm_hi;
+};
+__device__ __forceinline__ PlaneOffsets plane_offsets(const Geom& g, int m) {
+  const int ps = g.rows * g.pitch;
+  PlaneOffsets o;
+  o.dm_lo = m > 0 ? -ps : (g.per_m ? (g.nm - 1) * ps : 0);
+  o.dm_hi = m < g.nm - 1 ? ps : (g.per_m ? -(g.nm - 1) * ps : 0);
+  return o;
+}
+
+// Pull one cell (Eq. Stream, pull form).  Sources are the slot's wrap-aware in-plane offsets plus
+// the plane offsets; where the source is solid or beyond a wall the population leaving the cell
+// comes back reversed (halfway bounce-back).
 template <int Q, int S>
-__device__ __forceinline__ typename Storage<S>::real pull_exchange(
-    const StepArgs& A, const Slot& s, const Plane& p, int cell, uint32_t sbits,
-    V2<typename Storage<S>::real> (&g)[Q], typename Storage<S>::real& rr,
-    typename Storage<S>::real& rb, typename Storage<S>::real& e, uint32_t& flags) {
+__device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int si,
+                                          PlaneOffsets po, uint32_t sbits,
+                                          V2<typename Storage<S>::real> (&g)[Q]) {
   using L = Lattice<Q>;
   using IO = PopIO<S, Q>;
-  const Geom& G = A.g;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const int ca = L::ca(i), cb = L::cb(i), cm = L::cm(i);
-    const int as = ca > 0 ? s.am1 : (ca < 0 ? s.ap1 : s.a);
-    const int bs = cb > 0 ? s.bm1 : (cb < 0 ? s.bp1 : s.b);
-    const int ms = cm > 0 ? p.mm1 : (cm < 0 ? p.mp1 : p.m);
-    const bool bounce = (sbits >> i) & 1u;
-    const int src = bounce ? cell : (ms * G.nb + bs) * G.na + as;
-    const int dir = bounce ? opp(i) : i;
-    g[i] = IO::load(A.pin, G.ncell, i, dir, src, A.ph);
+    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+    int dir = i;
+    if (sbits) {
+      const bool bounce = (sbits >> i) & 1u;
+      src = bounce ? si : src;
+      dir = bounce ? opp(i) : i;
+    }
+    g[i] = IO::load(A.pin, A.g.nstore, i, dir, src, A.ph);
   }
-  return site_exchange<Q, S>(A, cell, g, rr, rb, e, flags);
 }
 
 template <class R>
@@ -179,13 +214,19 @@ __device__ __forceinline__ void norm_pair<float>(float F2, float& Fn, float& iFn
   Fn = F2 * iFn;
 }
 
-// Moments, Eq. (collision) with Eq. (feq), Eq. (perturb), Eq. (recolor); stores f^{k*}.
-// rnb[i] is rho^N at x + c_i (the cell's own value where that neighbour is solid).
+// Moments, Eq. (collision) with Eq. (feq), Eq. (perturb), Eq. (recolor); stores f^{k*} at the
+// cell's storage index si and its periodic ghost images si + dimg[j], j < nimg.
+// rnb[i] is rho^N at x + c_i (the cell's own value where that neighbour is solid).  The factors
+// that depend only on the speed class s = |c_i|^2 are formed once per cell:
+//   f_i^eq = rho (A_s + B_s abar) + rho W_s (3 cu + 9/2 cu^2 - 3/2 u^2)            (Eq. feq)
+//   (9/4)(sigma/tau)|F|[W_s (F.c_i)^2/|F|^2 - C_s] = kw_s (F.c_i)^2 - kc_s        (Eq. perturb)
+//   beta (rho_r rho_b / rho^2) cos(theta_i) f_i^eq(rho, 0) = kr_s (F.c_i)          (Eq. recolor)
 template <int Q, int S>
-__device__ __forceinline__ void collide_store(const StepArgs& A, int cell,
+__device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nimg, const int (&dimg)[3],
                                               const V2<typename Storage<S>::real> (&g)[Q],
                                               typename Storage<S>::real rr,
                                               typename Storage<S>::real rb,
+                                              typename Storage<S>::real irho,
                                               const typename Storage<S>::real (&rnb)[Q],
                                               typename Storage<S>::real& Fn_out) {
   using L = Lattice<Q>;
@@ -193,7 +234,6 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int cell,
   using IO = PopIO<S, Q>;
   const Physics& ph = A.ph;
   const R rho = rr + rb;
-  const R irho = R(1) / rho;
   const R wr = rr * irho, wb = rb * irho;
   R f[Q];
   R ja = R(0), jb = R(0), jm = R(0);
@@ -208,7 +248,7 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int cell,
     if (L::cm(i) < 0) jm -= f[i];
   }
   const R ua = ja * irho, ub = jb * irho, um = jm * irho;
-  const R uu = ua * ua + ub * ub + um * um;
+  const R uu15 = R(1.5) * (ua * ua + ub * ub + um * um);
   const R itau = wr * (R)ph.inv_tau_r + wb * (R)ph.inv_tau_b;  // harmonic mean of tau_k
   const R abar = wr * (R)ph.alpha_r + wb * (R)ph.alpha_b;
   // Eq. (cg): F = (1/c_s^2) sum_i W_i rho^N(x + c_i) c_i
@@ -228,36 +268,67 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int cell,
   if (F2 > R(0)) norm_pair<R>(F2, Fn, iFn);
   const R pamp = (R)ph.amp * itau;       // (9/4) sigma / tau
   const R rcol = (R)ph.beta * wr * wb;   // beta rho_r rho_b / rho^2
+  R restc[3], rwc[3], kw[3], kc[3], kr[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = c == 0 ? 0 : (c == 1 ? 1 : L::Q - 1);  // a direction of speed class c
+    restc[c] = rho * (R(L::A(i)) + R(L::B(i)) * abar);   // f_i^eq(rho, 0)
+    rwc[c] = rho * R(L::W(i));
+    kw[c] = pamp * R(L::W(i)) * iFn;
+    kc[c] = pamp * R(L::C(i)) * Fn;
+    kr[c] = rcol * iFn * R(inv_norm<L>(i)) * restc[c];
+  }
   V2<R> f0{R(0), R(0)};
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const R ca = R(L::ca(i)), cb = R(L::cb(i)), cm = R(L::cm(i));
-    const R cu = ca * ua + cb * ub + cm * um;
-    const R rest = rho * (R(L::A(i)) + R(L::B(i)) * abar);  // f_i^eq(rho, 0)
-    const R feq = rest + rho * R(L::W(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-    R fi = f[i] - itau * (f[i] - feq);
-    const R pc = ca * Fa + cb * Fb + cm * Fm;
-    fi += pamp * (R(L::W(i)) * pc * pc * iFn - R(L::C(i)) * Fn);
-    const R cosv = (i == 0) ? R(0) : pc * iFn * R(inv_norm<L>(i));
-    const R fr = wr * fi + rcol * cosv * rest;
+    const int c = L::speed2(i);
+    R cu = R(0), pc = R(0);
+    if (L::ca(i) > 0) { cu += ua; pc += Fa; }
+    if (L::ca(i) < 0) { cu -= ua; pc -= Fa; }
+    if (L::cb(i) > 0) { cu += ub; pc += Fb; }
+    if (L::cb(i) < 0) { cu -= ub; pc -= Fb; }
+    if (L::cm(i) > 0) { cu += um; pc += Fm; }
+    if (L::cm(i) < 0) { cu -= um; pc -= Fm; }
+    const R feq = fma(rwc[c], fma(cu, fma(R(4.5), cu, R(3)), -uu15), restc[c]);
+    R fi = fma(itau, feq - f[i], f[i]);                 // Eq. (collision)
+    fi = fma(kw[c], pc * pc, fi - kc[c]);               // Eq. (perturb)
+    const R fr = fma(wr, fi, kr[c] * pc);               // Eq. (recolor)
     const R fb = fi - fr;
     if (i == 0) f0 = {fr, fb};
-    IO::store(A.pout, A.g.ncell, i, cell, fr, fb, f0, ph);
+    IO::store(A.pout, A.g.nstore, i, si, fr, fb, f0, ph);
+    if (nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
+      for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, i, si + dimg[j], fr, fb, f0, ph);
+    }
   }
   Fn_out = Fn;
 }
 
-template <int Q, int S, int TX, int TY, int MINB>
+// Ghost images of the column (a, b): storage deltas (plane-invariant).
+__device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d)[3]) {
+  int da = 0, db = 0;
+  if (g.img_a) da = a < 2 ? g.na : (a >= g.na - 2 ? -g.na : 0);
+  if (g.img_b) db = b < 2 ? g.nb : (b >= g.nb - 2 ? -g.nb : 0);
+  int n = 0;
+  if (da) d[n++] = da;
+  if (db) d[n++] = db * g.pitch;
+  if (da && db) d[n++] = da + db * g.pitch;
+  return n;
+}
+
+// CPT cells per thread: thread (lx, ly) owns the columns (lx, ly + c TY), c < CPT, of a
+// TX x (TY CPT) tile, so its pulls of all CPT cells are in flight together.
+template <int Q, int S, int TX, int TY, int MINB, int CPT>
 __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_constant__ StepArgs A) {
   using L = Lattice<Q>;
   using R = typename Storage<S>::real;
   constexpr int NT = TX * TY;
+  constexpr int TH = TY * CPT;  // tile rows
   constexpr int HX = TX + 2;
-  constexpr int HY = L::D3 ? TY + 2 : 1;
+  constexpr int HY = L::D3 ? TH + 2 : 1;
   constexpr int OB = L::D3 ? 1 : 0;
-  constexpr int NH = HX * HY - TX * TY;
+  constexpr int NH = HX * HY - TX * TH;
   static_assert(NH <= NT, "one ring cell per thread at most");
-  static_assert(L::D3 || TY == 1, "D2Q9 tiles are one row");
+  static_assert(L::D3 || (TY == 1 && CPT == 1), "D2Q9 tiles are one row");
   __shared__ R ring[4][HY][HX];
   __shared__ double red_d[NT / 32];
   __shared__ long long red_n[NT / 32];
@@ -266,47 +337,69 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   const Geom& G = A.g;
   const int tid = threadIdx.x;
   const int a0 = (blockIdx.x % A.ntx) * TX;
-  const int b0 = (blockIdx.x / A.ntx) * TY;
+  const int b0 = (blockIdx.x / A.ntx) * TH;
   const int m0 = blockIdx.y * A.pc;
   const int m1 = min(m0 + A.pc, G.nm);
-  const int lx = tid % TX, ly = tid / TX;
-  const bool active = (a0 + lx < G.na) && (b0 + ly < G.nb);
-  const Slot me = make_slot<L>(G, a0 + lx, b0 + ly);
+  const int lx = tid % TX, ly0 = tid / TX;
+  bool active[CPT];
+  Slot me[CPT];
+  int dimg[CPT][3];
+  int nimg[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int ly = ly0 + c * TY;
+    active[c] = (a0 + lx < G.na) && (b0 + ly < G.nb);
+    me[c] = make_slot<L>(G, a0 + lx, b0 + ly);
+    dimg[c][0] = dimg[c][1] = dimg[c][2] = 0;
+    nimg[c] = active[c] ? image_deltas(G, me[c].a, me[c].b, dimg[c]) : 0;
+  }
 
-  // This thread's ring cell, if any.
+  // This thread's ring cell, if any (the first NH threads take one each).
   int hx = 0, hy = 0;
   const bool has_halo = tid < NH;
+  const int hh = tid;
   if (has_halo) {
     if (L::D3) {
-      if (tid < HX) {
-        hx = tid;
+      if (hh < HX) {
+        hx = hh;
         hy = 0;
-      } else if (tid < 2 * HX) {
-        hx = tid - HX;
+      } else if (hh < 2 * HX) {
+        hx = hh - HX;
         hy = HY - 1;
       } else {
-        const int k = tid - 2 * HX;
+        const int k = hh - 2 * HX;
         hx = (k & 1) ? HX - 1 : 0;
         hy = 1 + (k >> 1);
       }
     } else {
-      hx = tid == 0 ? 0 : HX - 1;
+      hx = hh == 0 ? 0 : HX - 1;
       hy = 0;
     }
   }
   const Slot hs = make_slot<L>(G, a0 + hx - 1, b0 + hy - OB);
 
-  V2<R> cur[Q], nxt[Q];
-  R cur_rr = R(0), cur_rb = R(0), cur_e = R(0);
-  uint32_t cur_flags = 0, cur_bits = 0;
-  bool cur_ok = false;
+  // Pulled, post-exchange populations of the next plane wait in thread-private columns of
+  // shared memory (only this thread reads or writes its columns, so no barrier guards them).
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+  Vec* parked = reinterpret_cast<Vec*>(dyn_smem);  // [CPT][Q][NT]
+
+  struct CellScalars {
+    R rr, rb, e, irho;
+    uint32_t flags, bits;
+    bool ok;
+  };
+  CellScalars cur[CPT], nxt[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), 0u, 0u, false};
   long long n_sites = 0;
   double removed = 0.0;
 
-  // rho^N of the own slot and the ring slot in plane um; own populations kept in `keep`.
-  auto fill_plane = [&](int um, V2<R>(&keep)[Q], R& k_rr, R& k_rb, R& k_e, uint32_t& k_flags,
-                        uint32_t& k_bits, bool& k_ok) {
+  // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
+  // post-exchange populations are returned in g.
+  auto fill_plane = [&](int um, CellScalars(&out)[CPT], V2<R>(&g)[CPT][Q]) {
     const Plane p = make_plane(G, um);
+    const PlaneOffsets po = plane_offsets(G, p.m);
     const int slot = (um - m0 + 1) & 3;
     if (has_halo) {
       const int cell = (p.m * G.nb + hs.b) * G.na + hs.a;
@@ -314,71 +407,96 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
       R rn = R(0);
       if (solid_bits<L>(G, hs, p, cell, bits)) {
         V2<R> tmp[Q];
-        R t_rr, t_rb, t_e;
+        R t_rr, t_rb, t_e, t_irho;
         uint32_t t_flags;
-        rn = pull_exchange<Q, S>(A, hs, p, cell, bits, tmp, t_rr, t_rb, t_e, t_flags);
+        pull_cell<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, tmp);
+        rn = site_exchange<Q, S>(A, cell, tmp, t_rr, t_rb, t_e, t_flags, t_irho);
       }
       ring[slot][hy][hx] = rn;
     }
-    {
-      const int cell = (p.m * G.nb + me.b) * G.na + me.a;
+    int cells[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {  // issue every load of every own cell first
+      cells[c] = (p.m * G.nb + me[c].b) * G.na + me[c].a;
       uint32_t bits = 0;
+      out[c].ok = solid_bits<L>(G, me[c], p, cells[c], bits);
+      out[c].bits = bits;
+      if (out[c].ok) pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
       R rn = R(0);
-      k_ok = solid_bits<L>(G, me, p, cell, bits);
-      if (k_ok) rn = pull_exchange<Q, S>(A, me, p, cell, bits, keep, k_rr, k_rb, k_e, k_flags);
-      k_bits = bits;
-      ring[slot][ly + OB][lx + 1] = rn;
+      if (out[c].ok)
+        rn = site_exchange<Q, S>(A, cells[c], g[c], out[c].rr, out[c].rb, out[c].e, out[c].flags,
+                                 out[c].irho);
+      ring[slot][ly0 + c * TY + OB][lx + 1] = rn;
     }
   };
 
   {
-    V2<R> tmp[Q];
-    R t_rr, t_rb, t_e;
-    uint32_t t_flags, t_bits;
-    bool t_ok;
-    fill_plane(m0 - 1, tmp, t_rr, t_rb, t_e, t_flags, t_bits, t_ok);
+    CellScalars t[CPT];
+    V2<R> g[CPT][Q];
+    fill_plane(m0 - 1, t, g);
   }
-  fill_plane(m0, cur, cur_rr, cur_rb, cur_e, cur_flags, cur_bits, cur_ok);
+  {
+    V2<R> g[CPT][Q];
+    fill_plane(m0, cur, g);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        Vec v;
+        v.x = g[c][i].r;
+        v.y = g[c][i].b;
+        parked[(c * Q + i) * NT + tid] = v;
+      }
+  }
 
   for (int m = m0; m < m1; ++m) {
-    R n_rr = R(0), n_rb = R(0), n_e = R(0);
-    uint32_t n_flags = 0, n_bits = 0;
-    bool n_ok = false;
-    fill_plane(m + 1, nxt, n_rr, n_rb, n_e, n_flags, n_bits, n_ok);
+    V2<R> g[CPT][Q];
+    fill_plane(m + 1, nxt, g);
     __syncthreads();
-    if (active && cur_ok) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      // plane m of cell c leaves its parking column, plane m+1 takes its place
+      V2<R> own[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const Vec v = parked[(c * Q + i) * NT + tid];
+        own[i] = {v.x, v.y};
+        Vec w;
+        w.x = g[c][i].r;
+        w.y = g[c][i].b;
+        parked[(c * Q + i) * NT + tid] = w;
+      }
+      if (!(active[c] && cur[c].ok)) continue;
+      const int ly = ly0 + c * TY;
       const int s0 = (m - m0 + 1) & 3;
-      const R own = ring[s0][ly + OB][lx + 1];
+      const R ownrn = ring[s0][ly + OB][lx + 1];
       R rnb[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int s = (m - m0 + 1 + L::cm(i)) & 3;
-        const bool solid_nb = (cur_bits >> opp(i)) & 1u;  // x + c_i is the source of opp(i)
-        rnb[i] = solid_nb ? own : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
+        const bool solid_nb = (cur[c].bits >> opp(i)) & 1u;  // x + c_i is the source of opp(i)
+        rnb[i] = solid_nb ? ownrn : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
       }
-      const Plane p = make_plane(G, m);
-      const int cell = (p.m * G.nb + me.b) * G.na + me.a;
+      const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
       R Fn;
-      collide_store<Q, S>(A, cell, cur, cur_rr, cur_rb, rnb, Fn);
-      uint32_t mb = cur_flags;
+      collide_store<Q, S>(A, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own, cur[c].rr,
+                          cur[c].rb, cur[c].irho, rnb, Fn);
+      uint32_t mb = cur[c].flags;
       if (A.ph.rule == 0) {
         const R d = Fn - (R)A.ph.threshold;
         mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
       }
       A.mask_out[cell] = (uint8_t)mb;
-      if (cur_flags & 1u) {
+      if (cur[c].flags & 1u) {
         ++n_sites;
-        removed += (double)cur_e;
+        removed += (double)cur[c].e;
       }
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
-    cur_rr = n_rr;
-    cur_rb = n_rb;
-    cur_e = n_e;
-    cur_flags = n_flags;
-    cur_bits = n_bits;
-    cur_ok = n_ok;
+    for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];
   }
 
   // ---- ledger: warp shuffle, block, then the last block folds all partials in order ----

@@ -1,23 +1,27 @@
-// step_bulk.cuh -- the fused timestep with a bulk-copy pipeline through shared memory.
+// step_tma.cuh -- the fused timestep with a TMA pipeline through shared memory.
 //
 // Same arithmetic as cg_step_kernel (step_kernel.cuh), different data movement:
-//   * one producer warp streams, for every plane the CTA pulls, the Q "source boxes" of that
-//     plane into a shared-memory stage with 1D bulk asynchronous copies (cp.async.bulk, the
-//     Blackwell bulk-copy engine), one copy per box row, completing on an mbarrier;
-//     box i holds f_i at plane m - c_i,m over rows b0-1-c_i,b .. b0+TY-c_i,b and columns
-//     a0-2 .. a0+TX+1, so every cell of the tile and of its one-cell ring finds its pulled
-//     population of direction i at (row, column) = (e_b, e_a + 1 - c_i,a) of box i;
-//   * rows that cross a periodic x edge are split into pieces at the edge (the pieces stay
-//     16-byte aligned because nx is even); rows or planes beyond a wall are not copied -- those
-//     links bounce back and read the cell's own population from global memory instead;
+//   * one producer thread streams, for every plane the CTA pulls, Q "source boxes" into a
+//     shared-memory stage with TMA tensor copies (cp.async.bulk.tensor, one per direction),
+//     completing on an mbarrier; box i holds f_i at plane m - c_i,m over lattice rows
+//     b0-1-c_i,b .. b0+TY-c_i,b and columns a0-2 .. a0+TX+1, so every cell of the tile and of its
+//     one-cell ring finds its pulled population of direction i at (row, column) =
+//     (e_b, e_a + 1 - c_i,a) of box i;
+//   * the populations are stored with two ghost columns (and, in 3D, rows) holding periodic
+//     images, so a box never wraps; parts of a box beyond the stored grid (ragged last tiles)
+//     are zero-filled by the TMA unit and never read; planes beyond a z wall are not copied;
+//     links into walls or solids bounce back and read the cell's own population from global
+//     memory;
 //   * NST stages are in flight; consumers release a stage (empty mbarrier, one arrival per
 //     consumer warp) once the plane it holds has been collided;
-//   * consumer warps compute rho^N of the tile plus ring into the 4-plane ring, synchronise on a
+//   * consumer warps compute rho^N of the tile plus ring into a 4-plane ring, synchronise on a
 //     named barrier (the producer never joins it), then collide the previous plane.
 // Every mbarrier wait is bounded (about two seconds of wall time); on timeout the thread sets
 // the step's status word and carries on, so the launch always ends and the host reports
 // CGEVAP_ERR_TIMEOUT.
 #pragma once
+
+#include <cuda.h>
 
 #include "step_kernel.cuh"
 
@@ -70,12 +74,23 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* st
   }
 }
 
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
+// TMA tensor load of one box: 3-D (x, plane, direction) for D2Q9, 4-D (x, row, plane,
+// direction) for D3Q19.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 
@@ -84,7 +99,7 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 }
 
 template <int Q, int S, int TX, int TY>
-struct BulkShape {
+struct BoxShape {
   using L = Lattice<Q>;
   using Vec = typename Storage<S>::vec;
   static constexpr int EX = TX + 2;               // tile + ring, columns
@@ -92,25 +107,29 @@ struct BulkShape {
   static constexpr int BW = TX + 4;               // box columns a0-2 .. a0+TX+1
   static constexpr int BR = EY;                   // box rows
   static constexpr int ROW_BYTES = BW * (int)sizeof(Vec);
-  static constexpr int STAGE_BYTES = Q * BR * ROW_BYTES;
+  static constexpr int BOX_BYTES = BR * ROW_BYTES;
+  static constexpr int BOX_SLOT = (BOX_BYTES + 127) / 128 * 128;  // TMA destinations: 128 B
+  static constexpr int STAGE_BYTES = Q * BOX_SLOT;
   static constexpr int NC = TX * TY;              // consumer threads
-  static_assert(ROW_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(ROW_BYTES % 16 == 0, "TMA box rows are multiples of 16 bytes");
+  static_assert(BW <= 256 && BR <= 256, "TMA box dimensions are at most 256");
 };
 
 template <int Q, int S, int TX, int TY, int NST>
-constexpr int bulk_smem_bytes() {
-  using B = BulkShape<Q, S, TX, TY>;
+constexpr int tma_smem_bytes() {
+  using B = BoxShape<Q, S, TX, TY>;
   using R = typename Storage<S>::real;
   return NST * B::STAGE_BYTES + 4 * B::EY * B::EX * (int)sizeof(R) + 2 * NST * 8 +
          (B::NC / 32) * 16 + 16;
 }
 
 template <int Q, int S, int TX, int TY, int NST>
-__global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __grid_constant__ StepArgs A) {
+__global__ void __launch_bounds__(TX* TY + 32, 1)
+    cg_step_tma_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CUtensorMap tmap) {
   using L = Lattice<Q>;
   using R = typename Storage<S>::real;
   using Vec = typename Storage<S>::vec;
-  using B = BulkShape<Q, S, TX, TY>;
+  using B = BoxShape<Q, S, TX, TY>;
   using IO = PopIO<S, Q>;
   constexpr int NC = B::NC;
   constexpr int EX = B::EX, EY = B::EY, OB = L::D3 ? 1 : 0;
@@ -146,61 +165,29 @@ __global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __gr
   double removed = 0.0;
 
   if (tid >= NC) {
-    // ------------------------------------------------------------------ producer warp ------
-    const int lane = tid - NC;
-    const uint32_t stage0 = smem_addr(stages);
-    const Vec* pops = reinterpret_cast<const Vec*>(A.pin);
-    for (int k = 0; k < NP; ++k) {
-      const int s = k % NST;
-      if (k >= NST) mbar_wait(empty0 + 8 * s, (uint32_t)((k / NST) - 1) & 1u, A.red.status);
-      const Plane pl = make_plane(G, m0 - 1 + k);
-      // Pass 1 counts this lane's bytes, pass 2 issues the copies.
-      uint32_t bytes = 0;
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
+    // ------------------------------------------------------------------ producer thread ----
+    if (tid == NC) {
+      const uint32_t stage0 = smem_addr(stages);
+      for (int k = 0; k < NP; ++k) {
+        const int s = k % NST;
+        if (k >= NST) mbar_wait(empty0 + 8 * s, (uint32_t)((k / NST) - 1) & 1u, A.red.status);
+        const Plane pl = make_plane(G, m0 - 1 + k);
+        int ms[Q];
+        uint32_t bytes = 0;
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) bytes += __shfl_down_sync(0xffffffffu, bytes, off);
-          if (lane == 0) mbar_expect_arrive(full0 + 8 * s, bytes);
-          __syncwarp();
+        for (int i = 0; i < Q; ++i) {
+          ms[i] = pl.ok ? step_coord(pl.m, -L::cm(i), G.nm, G.per_m) : -1;
+          if (ms[i] >= 0) bytes += B::BOX_BYTES;
         }
-        for (int row = lane; row < Q * B::BR && pl.ok; row += 32) {
-          const int i = row / B::BR, r = row % B::BR;
-          // source plane and row of box i
-          const int ms = step_coord(pl.m, -L::cm(i), G.nm, G.per_m);
-          if (ms < 0) continue;
-          int bs = 0;
-          if (L::D3) {
-            bs = step_coord(b0 - 1 - L::cb(i) + r, 0, G.nb, G.per_b);
-            if (bs < 0) continue;
-          }
-          const Vec* rowp = pops + (size_t)i * G.ncell + ((size_t)ms * G.nb + bs) * G.na;
-          const uint32_t dst_row = stage0 + s * B::STAGE_BYTES + (i * B::BR + r) * B::ROW_BYTES;
-          // columns a0-2 .. a0+TX+1, split where they cross the x edges
-          int c = 0;
-          while (c < B::BW) {
-            const int ux = a0 - 2 + c;
-            int len = B::BW - c;
-            int xw = ux;
-            bool skip = false;
-            if (ux < 0) {
-              if (G.per_a) xw = wrap(ux, G.na); else skip = true;
-              len = min(len, -ux);
-              if (G.per_a) len = min(len, G.na - xw);
-            } else if (ux >= G.na) {
-              if (G.per_a) xw = wrap(ux, G.na); else skip = true;
-              if (G.per_a) len = min(len, G.na - xw);
-            } else {
-              len = min(len, G.na - ux);
-            }
-            if (!skip) {
-              const uint32_t nb = (uint32_t)len * (uint32_t)sizeof(Vec);
-              if (pass == 0)
-                bytes += nb;
-              else
-                bulk_copy(dst_row + c * (int)sizeof(Vec), rowp + xw, nb, full0 + 8 * s);
-            }
-            c += len;
-          }
+        mbar_expect_arrive(full0 + 8 * s, bytes);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (ms[i] < 0) continue;
+          const uint32_t dst = stage0 + s * B::STAGE_BYTES + i * B::BOX_SLOT;
+          if (L::D3)
+            tma_load_4d(dst, &tmap, a0 + kOx - 2, b0 + 1 - L::cb(i), ms[i], i, full0 + 8 * s);
+          else
+            tma_load_3d(dst, &tmap, a0 + kOx - 2, ms[i], i, full0 + 8 * s);
         }
       }
     }
@@ -209,6 +196,8 @@ __global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __gr
     const int lx = tid % TX, ly = tid / TX;
     const bool active = (a0 + lx < G.na) && (b0 + ly < G.nb);
     const Slot me = make_slot<L>(G, a0 + lx, b0 + ly);
+    int dimg[3] = {0, 0, 0};
+    const int nimg = active ? image_deltas(G, me.a, me.b, dimg) : 0;
     for (int k = 0; k < NP; ++k) {
       const int s = k % NST;
       mbar_wait(full0 + 8 * s, (uint32_t)(k / NST) & 1u, A.red.status);
@@ -226,16 +215,16 @@ __global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __gr
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             if ((bits >> i) & 1u) {
-              g[i] = IO::load(A.pin, G.ncell, i, opp(i), cell, A.ph);
+              g[i] = IO::load(A.pin, G.nstore, i, opp(i), sidx(G, sl.a, sl.b, pl.m), A.ph);
             } else {
               const Vec v = *reinterpret_cast<const Vec*>(
-                  st + (i * B::BR + ey) * B::ROW_BYTES + (ex + 1 - L::ca(i)) * (int)sizeof(Vec));
+                  st + i * B::BOX_SLOT + ey * B::ROW_BYTES + (ex + 1 - L::ca(i)) * (int)sizeof(Vec));
               g[i] = {v.x, v.y};
             }
           }
-          R rr, rb, e;
+          R rr, rb, e, irho;
           uint32_t fl;
-          rn = site_exchange<Q, S>(A, cell, g, rr, rb, e, fl);
+          rn = site_exchange<Q, S>(A, cell, g, rr, rb, e, fl, irho);
         }
         ring[k & 3][ey][ex] = rn;
       }
@@ -252,16 +241,16 @@ __global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __gr
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             if ((bits >> i) & 1u) {
-              g[i] = IO::load(A.pin, G.ncell, i, opp(i), cell, A.ph);
+              g[i] = IO::load(A.pin, G.nstore, i, opp(i), sidx(G, me.a, me.b, pc.m), A.ph);
             } else {
               const Vec v = *reinterpret_cast<const Vec*>(
-                  sc + (i * B::BR + ly + OB) * B::ROW_BYTES + (lx + 2 - L::ca(i)) * (int)sizeof(Vec));
+                  sc + i * B::BOX_SLOT + (ly + OB) * B::ROW_BYTES + (lx + 2 - L::ca(i)) * (int)sizeof(Vec));
               g[i] = {v.x, v.y};
             }
           }
-          R rr, rb, e;
+          R rr, rb, e, irho;
           uint32_t fl;
-          site_exchange<Q, S>(A, cell, g, rr, rb, e, fl);
+          site_exchange<Q, S>(A, cell, g, rr, rb, e, fl, irho);
           const R own = ring[kc & 3][ly + OB][lx + 1];
           R rnb[Q];
 #pragma unroll
@@ -270,7 +259,7 @@ __global__ void __launch_bounds__(TX* TY + 32, 1) cg_step_bulk_kernel(const __gr
             rnb[i] = solid_nb ? own : ring[(kc + L::cm(i)) & 3][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
           }
           R Fn;
-          collide_store<Q, S>(A, cell, g, rr, rb, rnb, Fn);
+          collide_store<Q, S>(A, sidx(G, me.a, me.b, pc.m), nimg, dimg, g, rr, rb, irho, rnb, Fn);
           uint32_t mb = fl;
           if (A.ph.rule == 0) {
             const R d = Fn - (R)A.ph.threshold;

@@ -25,14 +25,14 @@ def oracle_run(case: inputs.Case, steps: int, phi_field=None, solid=None):
 
 
 def gpu_sim(case: inputs.Case, storage: str, phi_field=None, solid=None, kernel=None):
-    """A simulation on the GPU; storage may carry a kernel family as "f32:bulk" / "f32:reg"."""
+    """A simulation on the GPU; storage may carry a kernel family as "f32:tma" / "f32:reg"."""
     import torch
     from paper_2412_14859_gb300.binding import Sim
     if ":" in storage:
         storage, kernel = storage.split(":")
     sim = Sim.from_case(case, storage)
     if kernel is not None:
-        sim.tune({"reg": 0, "bulk": 1}[kernel])
+        sim.tune({"reg": 0, "tma": 1}[kernel])
     if solid is not None:
         sim.set_solid(torch.from_numpy(np.ascontiguousarray(solid, np.uint8)).cuda())
     if phi_field is not None:
