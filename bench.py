@@ -272,8 +272,7 @@ def run_ours(args, d: Dist):
         K = args.steps
         with torch.cuda.stream(stream):
             sim = Sim.from_case(case, st)
-            if st == "f32":
-                sim.tune(args.kernel, args.variant)
+            sim.tune(args.kernel if st == "f32" else 0, args.variant)
             sim.set_flux(case.phi)
             sim.init_equilibrium(rn, noise)
             sim.step(args.warmup)
@@ -332,8 +331,7 @@ def run_ours(args, d: Dist):
             f_host = sim.populations(torch.float32).cpu().pin_memory().numpy()
             sim.close()
             sim2 = Sim.from_case(case, head)
-            if head == "f32":
-                sim2.tune(args.kernel, args.variant)
+            sim2.tune(args.kernel if head == "f32" else 0, args.variant)
             sim2.set_flux(case.phi)
             sim2.set_populations_host(f_host)  # allocates the staging buffer once, untimed
             torch.cuda.synchronize()

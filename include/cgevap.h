@@ -168,7 +168,8 @@ CGEVAP_API int cgevap_check_health(cgevap_sim* sim);
 CGEVAP_API int cgevap_save(cgevap_sim* sim, const char* path);
 CGEVAP_API int cgevap_load(cgevap_sim* sim, const char* path);
 
-/* Select the fused-step kernel: family -1 automatic (the default at create), 0 the
+/* Select the fused-step kernel: family -1 automatic (the default at create: currently the
+ * register-pipelined kernel, measured faster), 0 the
  * register-pipelined kernel (every storage, any nx), 1 the bulk-copy pipelined kernel (FP32
  * storage and even nx); variant picks a tile shape / pipeline depth of that family (0 = default);
  * planes_per_chunk > 0 fixes how many planes one CTA marches through (0 = planner).  All

@@ -656,7 +656,7 @@ int cgevap_load(cgevap_sim* s, const char* path) {
 int cgevap_tune(cgevap_sim* s, int family, int variant, int planes_per_chunk) {
   if (!s) return CGEVAP_ERR_ARG;
   CG_CUDA(s, cudaSetDevice(s->device));
-  if (family < 0) family = tma_supported(s) ? 1 : 0;
+  if (family < 0) family = 0;  // the register-pipelined kernel is the faster one on GB300
   if (family > 1) return fail(s, CGEVAP_ERR_ARG, "kernel family must be -1, 0 or 1");
   if (family == 1 && !tma_supported(s))
     return fail(s, CGEVAP_ERR_UNSUPPORTED,

@@ -201,6 +201,50 @@ __device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int
   }
 }
 
+// Deviation storage: pull one cell whose source rest populations are staged in shared memory.
+// restbox(q, y, x) is the (f_0^r, f_0^b) pair of the cell at box row y, column x of plane slot q;
+// (ex, ey) is this cell's own box position and ps[k] the slot of plane m + 1 - k, so the source
+// plane m - c_m of direction i is ps[1 + c_m].
+template <int Q, int S, class RestBox>
+__device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl, int si,
+                                              PlaneOffsets po, uint32_t sbits, int ex, int ey,
+                                              const int (&ps)[3], const RestBox& restbox,
+                                              V2<float> (&g)[Q]) {
+  using L = Lattice<Q>;
+  using P = typename Storage<S>::packed;
+  const Physics& ph = A.ph;
+  const P* dev = reinterpret_cast<const P*>(reinterpret_cast<const char*>(A.pin) +
+                                            dev_block_offset(A.g.nstore));
+  uint32_t raw[Q];
+  // all deviation loads first
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+    int dir = i;
+    if (sbits) {
+      const bool bounce = (sbits >> i) & 1u;
+      src = bounce ? si : src;
+      dir = bounce ? opp(i) : i;
+    }
+    const P v = __ldg(dev + (size_t)(dir - 1) * A.g.nstore + src);
+    raw[i] = *reinterpret_cast<const uint32_t*>(&v);
+  }
+  const float2 r0 = restbox(ps[1], ey, ex);
+  g[0] = {r0.x, r0.y};
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const bool bounce = sbits && ((sbits >> i) & 1u);
+    // the source's rest pair: box position x - c_i in plane m - c_i,m (own cell if bounced)
+    const float2 rs = bounce ? r0 : restbox(ps[1 + L::cm(i)], ey - L::cb(i), ex - L::ca(i));
+    P pv;
+    *reinterpret_cast<uint32_t*>(&pv) = raw[i];
+    const float2 d = Storage<S>::unpack(pv);
+    g[i] = {fmaf(rs.x, ph.kap_r[i], d.x * ph.inv_scale), fmaf(rs.y, ph.kap_b[i], d.y * ph.inv_scale)};
+  }
+}
+
 template <class R>
 __device__ __forceinline__ void norm_pair(R F2, R& Fn, R& iFn);
 template <>
@@ -330,6 +374,14 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   static_assert(NH <= NT, "one ring cell per thread at most");
   static_assert(L::D3 || (TY == 1 && CPT == 1), "D2Q9 tiles are one row");
   __shared__ R ring[4][HY][HX];
+  // deviation storage: rest pairs of the tile plus a two-cell ring, planes m .. m+2
+  constexpr bool DEV = Storage<S>::dev;
+  constexpr int RX = DEV ? TX + 4 : 1;
+  constexpr int RY = DEV ? (L::D3 ? TH + 4 : 1) : 1;
+  constexpr int RS = DEV ? 3 : 1;
+  constexpr int RN = RX * RY;
+  constexpr int RPT = (RN + NT - 1) / NT;  // rest-box elements staged per thread
+  __shared__ float2 rest_ring[RS][RY][RX];
   __shared__ double red_d[NT / 32];
   __shared__ long long red_n[NT / 32];
   __shared__ int is_last;
@@ -378,6 +430,42 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   }
   const Slot hs = make_slot<L>(G, a0 + hx - 1, b0 + hy - OB);
 
+  // deviation storage: in-plane storage offsets of this thread's rest-box elements (-1: beyond a
+  // wall or not this thread's)
+  int rest_off[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    rest_off[k] = -1;
+    const int e = tid + k * NT;
+    if (DEV && e < RN) {
+      const int ex = e % RX, ey = e / RX;
+      int a = a0 - 2 + ex, b = L::D3 ? b0 - 2 + ey : 0;
+      bool ok = true;
+      if (a < 0 || a >= G.na) {
+        if (G.per_a) a = wrap(a, G.na); else ok = false;
+      }
+      if (L::D3 && (b < 0 || b >= G.nb)) {
+        if (G.per_b) b = wrap(b, G.nb); else ok = false;
+      }
+      if (ok) rest_off[k] = (b + G.gy) * G.pitch + a + kOx;
+    }
+  }
+  const int plane_stride = G.rows * G.pitch;
+  auto rest_slot = [&](int uq) { return (uq - m0 + 3) % 3; };
+  auto stage_rest = [&](int uq) {  // rest pairs of plane uq (unwrapped) into its slot
+    if (!DEV) return;
+    const Plane q = make_plane(G, uq);
+    const float2* rest = reinterpret_cast<const float2*>(A.pin);
+    const int sl = rest_slot(uq);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int e = tid + k * NT;
+      if (e < RN && q.ok && rest_off[k] >= 0)
+        rest_ring[sl][e / RX][e % RX] = __ldg(rest + q.m * plane_stride + rest_off[k]);
+    }
+  };
+  auto restbox = [&](int slot, int y, int x) -> float2 { return rest_ring[slot][y][x]; };
+
   // Pulled, post-exchange populations of the next plane wait in thread-private columns of
   // shared memory (only this thread reads or writes its columns, so no barrier guards them).
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -401,6 +489,14 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
     const Plane p = make_plane(G, um);
     const PlaneOffsets po = plane_offsets(G, p.m);
     const int slot = (um - m0 + 1) & 3;
+    int ps[3] = {0, 0, 0};
+    if (DEV) {  // the pulls of plane um read the rest pairs of planes um-1 .. um+1
+      stage_rest(um + 1);
+      __syncthreads();
+      ps[0] = rest_slot(um + 1);
+      ps[1] = rest_slot(um);
+      ps[2] = rest_slot(um - 1);
+    }
     if (has_halo) {
       const int cell = (p.m * G.nb + hs.b) * G.na + hs.a;
       uint32_t bits = 0;
@@ -409,7 +505,11 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
         V2<R> tmp[Q];
         R t_rr, t_rb, t_e, t_irho;
         uint32_t t_flags;
-        pull_cell<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, tmp);
+        if constexpr (DEV)
+          pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
+                              L::D3 ? hy + 1 : 0, ps, restbox, tmp);
+        else
+          pull_cell<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, tmp);
         rn = site_exchange<Q, S>(A, cell, tmp, t_rr, t_rb, t_e, t_flags, t_irho);
       }
       ring[slot][hy][hx] = rn;
@@ -421,7 +521,13 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
       uint32_t bits = 0;
       out[c].ok = solid_bits<L>(G, me[c], p, cells[c], bits);
       out[c].bits = bits;
-      if (out[c].ok) pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
+      if (out[c].ok) {
+        if constexpr (DEV)
+          pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
+                              L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c]);
+        else
+          pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
@@ -433,11 +539,14 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
     }
   };
 
+  stage_rest(m0 - 2);
+  stage_rest(m0 - 1);
   {
     CellScalars t[CPT];
     V2<R> g[CPT][Q];
     fill_plane(m0 - 1, t, g);
   }
+  __syncthreads();  // the next fill restages a rest slot the pulls above may still read
   {
     V2<R> g[CPT][Q];
     fill_plane(m0, cur, g);
@@ -451,6 +560,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
         parked[(c * Q + i) * NT + tid] = v;
       }
   }
+  if (DEV) __syncthreads();  // the first fill below restages a rest slot the pulls above read
 
   for (int m = m0; m < m1; ++m) {
     V2<R> g[CPT][Q];
