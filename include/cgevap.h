@@ -187,6 +187,46 @@ CGEVAP_API double cgevap_bytes_per_update(const cgevap_sim* sim);
 /* Number of fluid cells. */
 CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
 
+/* ---- ensembles: many independent lattices in one persistent launch ---------------------------
+ * An ensemble advances n independent members (D2Q9 and D3Q19 lattices of any sizes, each with its
+ * own densities, relaxation times, surface tension, recoloring, site rule, threshold, S-bar,
+ * flux and solids; FP32 storage) by one cooperative persistent kernel launch per call, captured
+ * once in a CUDA graph and replayed.  Each member is a full cgevap_sim reachable with
+ * cgevap_ensemble_member: set its flux, solids and initial state, read its macros, mask and
+ * ledger with the single-lattice calls; cgevap_ensemble_step advances all of them together and
+ * gives the same result per member as cgevap_step on that member alone. */
+typedef struct cgevap_ens cgevap_ens;
+
+/* Create members[0..n-1] (each validated like cgevap_create; storage must be CGEVAP_F32, else
+ * UNSUPPORTED) and plan the work list with a default tiling.  *out is NULL on failure. */
+CGEVAP_API int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out);
+/* Free the ensemble and all its members.  NULL is accepted. */
+CGEVAP_API int cgevap_ensemble_destroy(cgevap_ens* ens);
+/* Message for the last failure on ens; never NULL. */
+CGEVAP_API const char* cgevap_ensemble_last_error(const cgevap_ens* ens);
+/* Number of members / total cells of all members. */
+CGEVAP_API int cgevap_ensemble_size(const cgevap_ens* ens);
+CGEVAP_API long long cgevap_ensemble_cells(const cgevap_ens* ens);
+/* Handle of member j (owned by the ensemble; do not destroy it or change its stream). */
+CGEVAP_API int cgevap_ensemble_member(cgevap_ens* ens, int j, cgevap_sim** out);
+/* Stream for the ensemble and all its members (NULL = legacy default stream). */
+CGEVAP_API int cgevap_ensemble_set_stream(cgevap_ens* ens, void* cuda_stream);
+/* Advance every member by nsteps >= 0 in one cooperative launch (graph-captured per nsteps and
+ * replayed).  Asynchronous; cgevap_ensemble_status reports a grid barrier that gave up. */
+CGEVAP_API int cgevap_ensemble_step(cgevap_ens* ens, int nsteps);
+/* CGEVAP_ERR_TIMEOUT if a bounded grid barrier gave up since the last call (flag cleared), else
+ * OK; synchronises the stream. */
+CGEVAP_API int cgevap_ensemble_status(cgevap_ens* ens);
+/* Tiling of the work list: D2Q9 tiles per CTA (2 or 4, i.e. rows of 128 or 64 cells) and planes
+ * per chunk for D3Q19 and D2Q9 members. */
+CGEVAP_API int cgevap_ensemble_set_tuning(cgevap_ens* ens, int groups, int planes_3d, int planes_2d);
+CGEVAP_API int cgevap_ensemble_get_tuning(const cgevap_ens* ens, int* groups, int* planes_3d,
+                                          int* planes_2d);
+/* Autotuner: times probe_steps steps of every candidate tiling on the ensemble as it is (its
+ * states, site bytes and ledgers are backed up first and restored after), keeps the fastest and
+ * writes its time per step to *best_ms (may be NULL).  Needs room for one copy of the states. */
+CGEVAP_API int cgevap_ensemble_autotune(cgevap_ens* ens, int probe_steps, double* best_ms);
+
 /* ---- one timestep without any allocation -------------------------------------------------
  * No counterpart in the paper; it serves callers that cannot allocate device memory: code running
  * inside a framework that owns every buffer and forbids allocation in its operators (a custom

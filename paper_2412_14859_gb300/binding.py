@@ -78,6 +78,19 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cgevap_step_static_scratch": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_double, _vp,
                                                   _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]),
+    "cgevap_ensemble_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(_vp)]),
+    "cgevap_ensemble_destroy": (ctypes.c_int, [_vp]),
+    "cgevap_ensemble_last_error": (ctypes.c_char_p, [_vp]),
+    "cgevap_ensemble_size": (ctypes.c_int, [_vp]),
+    "cgevap_ensemble_cells": (ctypes.c_longlong, [_vp]),
+    "cgevap_ensemble_member": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "cgevap_ensemble_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_ensemble_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cgevap_ensemble_status": (ctypes.c_int, [_vp]),
+    "cgevap_ensemble_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cgevap_ensemble_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cgevap_ensemble_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -117,6 +130,8 @@ def _dt(t: torch.Tensor) -> int:
 class Sim:
     """One lattice on the current CUDA device (a handle of the C ABI)."""
 
+    _borrowed = False
+
     def __init__(self, q: int, nx: int, ny: int, nz: int = 1, periodic=(1, 1, 1),
                  rho_r_in: float = 1.0, rho_b_in: float = 1.0, tau_r: float = 1.0,
                  tau_b: float = 1.0, sigma: float = 0.0, beta: float = 0.7,
@@ -150,9 +165,22 @@ class Sim:
         self._check(lib().cgevap_set_stream(self._h, s))
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and not self._borrowed:
             lib().cgevap_destroy(self._h)
-            self._h = None
+        self._h = None
+
+    @classmethod
+    def _wrap(cls, handle, params: Params, owner) -> "Sim":
+        """A member of an ensemble: the ensemble owns (and frees) the handle."""
+        obj = cls.__new__(cls)
+        obj.params = params
+        obj.q = params.q
+        obj.shape = (params.nz, params.ny, params.nx)
+        obj.ncell = params.nx * params.ny * params.nz
+        obj._h = handle
+        obj._borrowed = True
+        obj._owner = owner
+        return obj
 
     def __del__(self):
         try:
@@ -261,3 +289,75 @@ class Sim:
 def all_signatures():
     """Names of the C functions this binding declares (kept equal to include/*.h by a test)."""
     return list(_SIGS)
+
+
+class Ensemble:
+    """Independent lattices advanced together by one persistent launch (FP32 storage)."""
+
+    def __init__(self, cases):
+        arr = (Params * len(cases))()
+        for j, c in enumerate(cases):
+            nz, ny, nx = c.shape
+            arr[j] = Params(c.q, nx, ny, nz, (ctypes.c_int * 3)(*c.periodic), c.rho_r_in,
+                            c.rho_b_in, c.tau_r, c.tau_b, c.sigma, c.beta, c.site_rule,
+                            c.threshold, c.sbar, F32)
+        h = _vp()
+        rc = lib().cgevap_ensemble_create(arr, len(cases), ctypes.byref(h))
+        if rc != 0:
+            raise CgevapError(rc, "cgevap_ensemble_create failed")
+        self._h = h
+        self._params = [arr[j] for j in range(len(cases))]
+        self.members = []
+        for j in range(len(cases)):
+            mh = _vp()
+            self._check(lib().cgevap_ensemble_member(self._h, j, ctypes.byref(mh)))
+            self.members.append(Sim._wrap(mh, self._params[j], self))
+        self._sync_stream()
+
+    def _check(self, rc):
+        if rc != 0:
+            raise CgevapError(rc, lib().cgevap_ensemble_last_error(self._h).decode())
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream().cuda_stream
+        self._check(lib().cgevap_ensemble_set_stream(self._h, s))
+
+    def step(self, n: int = 1):
+        self._sync_stream()
+        self._check(lib().cgevap_ensemble_step(self._h, int(n)))
+        return self
+
+    def status(self):
+        self._check(lib().cgevap_ensemble_status(self._h))
+
+    @property
+    def cells(self) -> int:
+        return lib().cgevap_ensemble_cells(self._h)
+
+    def tuning(self) -> dict:
+        g, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().cgevap_ensemble_get_tuning(self._h, ctypes.byref(g), ctypes.byref(a),
+                                                     ctypes.byref(b)))
+        return {"groups": g.value, "planes_3d": a.value, "planes_2d": b.value}
+
+    def set_tuning(self, groups: int, planes_3d: int, planes_2d: int):
+        self._check(lib().cgevap_ensemble_set_tuning(self._h, groups, planes_3d, planes_2d))
+
+    def autotune(self, probe_steps: int = 4) -> float:
+        self._sync_stream()
+        ms = ctypes.c_double()
+        self._check(lib().cgevap_ensemble_autotune(self._h, probe_steps, ctypes.byref(ms)))
+        return ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            lib().cgevap_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -274,6 +274,36 @@ void release(cgevap_sim* s) {
 
 }  // namespace
 
+namespace cgevap {
+// Internal view of a simulation for the ensemble driver (same library, not exported).
+struct SimView {
+  Geom g;
+  Physics ph;
+  void* state[2];
+  uint8_t* mask[2];
+  DevLedger* ledger;
+  int* cur;
+  cudaStream_t* stream;
+  size_t state_bytes;
+  long long ncell;
+};
+int sim_view(cgevap_sim* s, SimView* v) {
+  if (!s || !v) return CGEVAP_ERR_ARG;
+  v->g = s->geom;
+  v->ph = s->ph;
+  v->state[0] = s->state[0];
+  v->state[1] = s->state[1];
+  v->mask[0] = s->mask[0];
+  v->mask[1] = s->mask[1];
+  v->ledger = s->ledger;
+  v->cur = &s->cur;
+  v->stream = &s->stream;
+  v->state_bytes = s->state_bytes;
+  v->ncell = s->N;
+  return CGEVAP_OK;
+}
+}  // namespace cgevap
+
 extern "C" {
 
 int cgevap_create(const cgevap_params* p, cgevap_sim** out) {

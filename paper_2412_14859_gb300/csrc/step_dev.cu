@@ -7,7 +7,7 @@ namespace cgevap {
 // Generic register-pipelined kernel (one cell per thread, decoded pairs parked).
 template <int Q, int S, int TX, int TY, int MINB, int CPT>
 static KernelRef reg_ref() {
-  constexpr int smem = CPT * Q * TX * TY * 8;
+  constexpr int smem = TileSmem<Q, S, TX, TY, CPT>::BYTES;
   const void* fn = (const void*)cg_step_kernel<Q, S, TX, TY, MINB, CPT>;
   static bool attr = false;
   if (!attr) {

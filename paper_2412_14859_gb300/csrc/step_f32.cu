@@ -6,7 +6,7 @@ namespace cgevap {
 
 template <int Q, int TX, int TY, int MINB, int CPT>
 static KernelRef reg_ref() {
-  constexpr int smem = CPT * Q * TX * TY * 8;
+  constexpr int smem = TileSmem<Q, ST_F32, TX, TY, CPT>::BYTES;
   const void* fn = (const void*)cg_step_kernel<Q, ST_F32, TX, TY, MINB, CPT>;
   static bool attr = false;
   if (!attr) {

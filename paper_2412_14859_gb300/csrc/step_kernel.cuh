@@ -359,10 +359,38 @@ __device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d
   return n;
 }
 
-// CPT cells per thread: thread (lx, ly) owns the columns (lx, ly + c TY), c < CPT, of a
-// TX x (TY CPT) tile, so its pulls of all CPT cells are in flight together.
-template <int Q, int S, int TX, int TY, int MINB, int CPT>
-__global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_constant__ StepArgs A) {
+// Shared-memory footprint of step_tile: the rho^N ring, the deviation storages' rest ring and
+// the parking columns (bytes).
+template <int Q, int S, int TX, int TY, int CPT>
+struct TileSmem {
+  using L = Lattice<Q>;
+  using R = typename Storage<S>::real;
+  static constexpr int TH = TY * CPT;
+  static constexpr int HX = TX + 2, HY = L::D3 ? TH + 2 : 1;
+  static constexpr bool DEV = Storage<S>::dev;
+  static constexpr int RX = DEV ? TX + 4 : 1, RY = DEV ? (L::D3 ? TH + 4 : 1) : 1, RS = DEV ? 3 : 1;
+  static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
+  static constexpr int REST = RS * RY * RX * 8;
+  static constexpr int PARK = CPT * Q * TX * TY * (int)(sizeof(R) == 8 ? 16 : 8);
+  static constexpr int BYTES = RING + REST + PARK;
+};
+
+// One CTA's work of the fused step: tile `tile` of the (a, b) plane, planes of chunk `chunk`
+// along m.  CPT cells per thread: thread (lx, ly) owns the columns (lx, ly + c TY), c < CPT, of a
+// TX x (TY CPT) tile, so its pulls of all CPT cells are in flight together.  smem points to
+// TileSmem<...>::BYTES bytes of shared memory.  Returns this thread's site count and removed mass.
+// tid: this thread's index within the TX*TY threads that run the tile; iters >= the number of
+// planes of the chunk: the loop runs that many barrier rounds (the extra ones idle), so several
+// tiles with different chunk lengths can share one CTA's barriers.
+template <int Q, int S, int TX, int TY, int CPT>
+__device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk, unsigned char* smem,
+                                          long long& n_sites, double& removed,
+                                          int tid = threadIdx.x, int iters = -1) {
+  using SM = TileSmem<Q, S, TX, TY, CPT>;
+  unsigned char* ring_mem = smem;
+  unsigned char* rest_mem = smem + SM::RING;
+  unsigned char* park_mem = smem + SM::RING + SM::REST;
+
   using L = Lattice<Q>;
   using R = typename Storage<S>::real;
   constexpr int NT = TX * TY;
@@ -373,7 +401,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   constexpr int NH = HX * HY - TX * TH;
   static_assert(NH <= NT, "one ring cell per thread at most");
   static_assert(L::D3 || (TY == 1 && CPT == 1), "D2Q9 tiles are one row");
-  __shared__ R ring[4][HY][HX];
+  R(*ring)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ring_mem);
   // deviation storage: rest pairs of the tile plus a two-cell ring, planes m .. m+2
   constexpr bool DEV = Storage<S>::dev;
   constexpr int RX = DEV ? TX + 4 : 1;
@@ -381,16 +409,12 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   constexpr int RS = DEV ? 3 : 1;
   constexpr int RN = RX * RY;
   constexpr int RPT = (RN + NT - 1) / NT;  // rest-box elements staged per thread
-  __shared__ float2 rest_ring[RS][RY][RX];
-  __shared__ double red_d[NT / 32];
-  __shared__ long long red_n[NT / 32];
-  __shared__ int is_last;
+  float2(*rest_ring)[RY][RX] = reinterpret_cast<float2(*)[RY][RX]>(rest_mem);
 
   const Geom& G = A.g;
-  const int tid = threadIdx.x;
-  const int a0 = (blockIdx.x % A.ntx) * TX;
-  const int b0 = (blockIdx.x / A.ntx) * TH;
-  const int m0 = blockIdx.y * A.pc;
+  const int a0 = (tile % A.ntx) * TX;
+  const int b0 = (tile / A.ntx) * TH;
+  const int m0 = chunk * A.pc;
   const int m1 = min(m0 + A.pc, G.nm);
   const int lx = tid % TX, ly0 = tid / TX;
   bool active[CPT];
@@ -468,9 +492,8 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
 
   // Pulled, post-exchange populations of the next plane wait in thread-private columns of
   // shared memory (only this thread reads or writes its columns, so no barrier guards them).
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
-  Vec* parked = reinterpret_cast<Vec*>(dyn_smem);  // [CPT][Q][NT]
+  Vec* parked = reinterpret_cast<Vec*>(park_mem);  // [CPT][Q][NT]
 
   struct CellScalars {
     R rr, rb, e, irho;
@@ -480,8 +503,8 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   CellScalars cur[CPT], nxt[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), 0u, 0u, false};
-  long long n_sites = 0;
-  double removed = 0.0;
+  n_sites = 0;
+  removed = 0.0;
 
   // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
   // post-exchange populations are returned in g.
@@ -562,7 +585,12 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
   }
   if (DEV) __syncthreads();  // the first fill below restages a rest slot the pulls above read
 
-  for (int m = m0; m < m1; ++m) {
+  const int m_end = iters < 0 ? m1 : m0 + iters;
+  for (int m = m0; m < m_end; ++m) {
+    if (m >= m1) {  // idle barrier rounds of a shorter chunk sharing the CTA
+      __syncthreads();
+      continue;
+    }
     V2<R> g[CPT][Q];
     fill_plane(m + 1, nxt, g);
     __syncthreads();
@@ -609,56 +637,85 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_cons
     for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];
   }
 
-  // ---- ledger: warp shuffle, block, then the last block folds all partials in order ----
+}
+
+// Block-wide sum of (n_sites, removed) into thread 0 (warp shuffles, then shared memory).
+template <int NT>
+__device__ __forceinline__ void block_sum(long long& n, double& d) {
+  __shared__ double red_d[NT / 32];
+  __shared__ long long red_n[NT / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    n_sites += __shfl_down_sync(0xffffffffu, n_sites, off);
-    removed += __shfl_down_sync(0xffffffffu, removed, off);
+    n += __shfl_down_sync(0xffffffffu, n, off);
+    d += __shfl_down_sync(0xffffffffu, d, off);
   }
+  const int tid = threadIdx.x;
   if ((tid & 31) == 0) {
-    red_d[tid >> 5] = removed;
-    red_n[tid >> 5] = n_sites;
+    red_d[tid >> 5] = d;
+    red_n[tid >> 5] = n;
   }
   __syncthreads();
-  const unsigned nblk = gridDim.x * gridDim.y;
   if (tid == 0) {
     double s = 0.0;
-    long long n = 0;
+    long long c = 0;
     for (int w = 0; w < NT / 32; ++w) {
       s += red_d[w];
-      n += red_n[w];
+      c += red_n[w];
     }
+    d = s;
+    n = c;
+  }
+  __syncthreads();
+}
+
+// Ledger fold: per-block partials, then the last block to arrive adds them, in block order, to
+// the device ledger (deterministic).
+__device__ __forceinline__ void ledger_fold(const Reduce& red, long long n, double d) {
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  if (tid == 0) {
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-    A.red.part_removed[bid] = s;
-    A.red.part_sites[bid] = n;
+    red.part_removed[bid] = d;
+    red.part_sites[bid] = n;
     __threadfence();
-    const unsigned prev = atomicAdd(A.red.done, 1u);
+    const unsigned prev = atomicAdd(red.done, 1u);
     is_last = (prev == nblk - 1);
   }
   __syncthreads();
   if (is_last && tid < 32) {
     __threadfence();
     double s = 0.0;
-    long long n = 0;
+    long long c = 0;
     for (unsigned j = tid; j < nblk; j += 32) {
-      s += __ldcg(A.red.part_removed + j);
-      n += __ldcg(A.red.part_sites + j);
+      s += __ldcg(red.part_removed + j);
+      c += __ldcg(red.part_sites + j);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       s += __shfl_down_sync(0xffffffffu, s, off);
-      n += __shfl_down_sync(0xffffffffu, n, off);
+      c += __shfl_down_sync(0xffffffffu, c, off);
     }
     if (tid == 0) {
-      DevLedger* led = A.red.ledger;
+      DevLedger* led = red.ledger;
       led->evaporated += s;
       led->last_removed = s;
-      led->site_steps += n;
-      led->last_sites = n;
+      led->site_steps += c;
+      led->last_sites = c;
       led->steps += 1;
-      *A.red.done = 0u;
+      *red.done = 0u;
     }
   }
+}
+
+template <int Q, int S, int TX, int TY, int MINB, int CPT>
+__global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_constant__ StepArgs A) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  long long n = 0;
+  double d = 0.0;
+  step_tile<Q, S, TX, TY, CPT>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d);
+  block_sum<TX * TY>(n, d);
+  ledger_fold(A.red, n, d);
 }
 
 }  // namespace cgevap
