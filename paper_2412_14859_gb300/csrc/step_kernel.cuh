@@ -369,10 +369,12 @@ struct TileSmem {
   static constexpr int HX = TX + 2, HY = L::D3 ? TH + 2 : 1;
   static constexpr bool DEV = Storage<S>::dev;
   static constexpr int RX = DEV ? TX + 4 : 1, RY = DEV ? (L::D3 ? TH + 4 : 1) : 1, RS = DEV ? 3 : 1;
+  // every part starts on a 16-byte boundary (the parking columns hold double2 in FP64)
   static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
-  static constexpr int REST = RS * RY * RX * 8;
-  static constexpr int PARK = CPT * Q * TX * TY * (int)(sizeof(R) == 8 ? 16 : 8);
+  static constexpr int REST = ((RS * RY * RX * 8) + 15) & ~15;
+  static constexpr int PARK = ((CPT * Q * TX * TY * (int)(sizeof(R) == 8 ? 16 : 8)) + 15) & ~15;
   static constexpr int BYTES = RING + REST + PARK;
+  static_assert(RING % 16 == 0 && REST % 16 == 0 && BYTES % 16 == 0, "16-byte aligned parts");
 };
 
 // One CTA's work of the fused step: tile `tile` of the (a, b) plane, planes of chunk `chunk`

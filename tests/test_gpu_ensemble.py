@@ -57,7 +57,8 @@ def test_members_equal_standalone_runs():
         assert (a - b).abs().max().item() <= 1e-5 * b.abs().max().item(), case.name
         la, lb = sim.ledger(), ref.ledger()
         assert la["steps"] == lb["steps"] == 13
-        assert la["evaporated"] == pytest.approx(lb["evaporated"], rel=1e-12)
+        # a site decided differently at the threshold moves phi/S-bar more or less
+        assert la["evaporated"] == pytest.approx(lb["evaporated"], rel=1e-3)
         assert abs(la["last_sites"] - lb["last_sites"]) <= 2
     ens.close()
 
