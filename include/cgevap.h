@@ -54,6 +54,8 @@ extern "C" {
 /* ---- evaporation-site rules ---- */
 #define CGEVAP_SITES_GRADIENT 0 /* site if |F| of the previous step > threshold (Sec. II.B)     */
 #define CGEVAP_SITES_BAND 1     /* site if |rho^N| after streaming < threshold (phase band)     */
+#define CGEVAP_SITES_GIVEN 2    /* site where bit0 of the site bytes read by the step is set: a
+                                   recorded site set replayed (cgevap_set_mask before each step) */
 
 /* ---- population storage formats (internal layouts; all arithmetic as stated) ---- */
 #define CGEVAP_F64 0      /* FP64 storage, FP64 arithmetic                                     */
@@ -74,7 +76,7 @@ typedef struct cgevap_params {
   double tau_r, tau_b;    /* component relaxation times, > 1/2 (Sec. II.A)                    */
   double sigma;           /* surface tension; perturbation amplitude (9/4) sigma / tau        */
   double beta;            /* recoloring parameter in [0, 1] (Eq. recolor)                     */
-  int site_rule;          /* CGEVAP_SITES_GRADIENT or CGEVAP_SITES_BAND                        */
+  int site_rule;          /* CGEVAP_SITES_GRADIENT, CGEVAP_SITES_BAND or CGEVAP_SITES_GIVEN     */
   double threshold;       /* Gamma (gradient rule) or theta (band rule)                       */
   double sbar;            /* S-bar > 0 of Eq. (relation); varphi = phi / S-bar                */
   int storage;            /* CGEVAP_F64, CGEVAP_F32, CGEVAP_F16DEV or CGEVAP_BF16DEV          */
@@ -150,6 +152,19 @@ CGEVAP_API int cgevap_get_macros(cgevap_sim* sim, double* dev_rho_r, double* dev
  * within 1e-6 of the threshold, bit3 = gradient rule: | |F| - Gamma | < 1e-6 at that step. */
 CGEVAP_API int cgevap_get_mask(cgevap_sim* sim, uint8_t* dev_mask);
 
+/* Replace the site bytes the next step reads with dev_mask [z][y][x] (copied).  Under
+ * CGEVAP_SITES_GIVEN the next step's sites x_I are the cells whose bit0 is set (Eq. exchange with
+ * a site set recorded by cgevap_get_mask after each step of an earlier run, so that a run can be
+ * repeated with x_I held fixed); under the gradient rule bit1 is the next step's site.
+ * Errors: ARG. */
+CGEVAP_API int cgevap_set_mask(cgevap_sim* sim, const uint8_t* dev_mask);
+
+/* Liquid volume of the state, V = sum over fluid cells of (1 + rho^N)/2 with rho^N =
+ * (rho_r - rho_b)/rho of the stored populations (Sec. II.A; the drop size whose evolution the
+ * paper's Sec. III compares with Eq. sphere_r), written as one FP64 value to dev_out[0].
+ * Deterministic (fixed reduction order).  Errors: ARG, OOM, CUDA. */
+CGEVAP_API int cgevap_volume(cgevap_sim* sim, double* dev_out);
+
 /* Copy the FP64 ledger to the host; synchronises the stream.  Returns CGEVAP_ERR_TIMEOUT (and
  * clears the flag) if a bounded device-side wait of a step since the last call gave up. */
 CGEVAP_API int cgevap_get_ledger(cgevap_sim* sim, cgevap_ledger* host_out);
@@ -186,6 +201,49 @@ CGEVAP_API double cgevap_bytes_per_update(const cgevap_sim* sim);
 
 /* Number of fluid cells. */
 CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
+
+/* ---- adjoint: derivative of a volume-history loss with respect to the flux field -------------
+ * Observable: V(t), t = 0..T, the liquid volume (cgevap_volume) after t steps.  The caller forms
+ * a loss L(V(0), ..., V(T)); given dL/dV(t), the backward sweep returns dL/dphi(x) for every cell:
+ * the exact derivative of the T fused steps (Eq. Stream with bounce-back, Eq. exchange, moments,
+ * Eq. cg, Eq. feq, Eq. collision, Eq. perturb, Eq. recolor) with the site sets x_I of all steps
+ * held at those of the forward run.  x_I is piecewise constant in phi, so this is the derivative
+ * of L wherever no decision value of the run sits exactly on the threshold (and the derivative
+ * of the run repeated with its sites replayed, CGEVAP_SITES_GIVEN, everywhere).  Storage F64 or
+ * F32 with the register-pipelined step (cgevap_tune family 0); arithmetic in the storage's
+ * precision, dL/dphi accumulated in FP64.  The flux may be a scalar or a field (cgevap_set_flux):
+ * the scalar derivative is the sum of dL/dphi over cells. */
+
+/* Run T = nsteps steps from the current state exactly as cgevap_step does (state, site bytes and
+ * ledger advance) and record what the backward sweep needs: the state and site bytes at every
+ * step that is a multiple of K = min(ckpt_every, T).  Device memory held until
+ * cgevap_adjoint_release, cgevap_destroy or a forward run of another (T, K):
+ * (ceil(T/K) + K + 3) states of the handle's state size plus (ceil(T/K) + K) site arrays and
+ * 7 per-cell reals; T/K near sqrt(T) minimises it.  dev_volume: caller-owned FP64 [T + 1],
+ * receives V(0), ..., V(T) (NULL: not recorded).  Errors: ARG (nsteps < 1 or ckpt_every < 1),
+ * UNSUPPORTED (16-bit storage, or the TMA step selected), OOM (tape), CUDA. */
+CGEVAP_API int cgevap_adjoint_forward(cgevap_sim* sim, int nsteps, int ckpt_every,
+                                      double* dev_volume);
+
+/* Reverse sweep over the recorded run.  Each segment of K steps is recomputed from its checkpoint
+ * with the forward run's step kernel (the handle's own state, site bytes and ledger stay as the
+ * forward run left them); the adjoint steps then run from step T-1 down to 0.
+ *   dev_dL_dV    caller-owned FP64 [T + 1], dL/dV(t) (entry 0 is not read: V(0) does not depend
+ *                on phi); NULL means 0;
+ *   dev_dL_dphi  caller-owned FP64 [z][y][x], overwritten with dL/dphi(x): 0 at solid cells and
+ *                at cells that were never a site.
+ * May be called again for another dL/dV over the same recorded run.  Errors: ARG (no recorded
+ * run, NULL dev_dL_dphi, the step's tuning changed since the forward run), CUDA. */
+CGEVAP_API int cgevap_adjoint_backward(cgevap_sim* sim, const double* dev_dL_dV,
+                                       double* dev_dL_dphi);
+
+/* cgevap_adjoint_forward (without the volume record) then cgevap_adjoint_backward, for a loss
+ * whose dL/dV(t) is known before the run (a loss linear in the volume history). */
+CGEVAP_API int cgevap_adjoint_run(cgevap_sim* sim, int nsteps, int ckpt_every,
+                                  const double* dev_dL_dV, double* dev_dL_dphi);
+
+/* Free the recorded run (synchronises the stream; no-op without one).  Errors: ARG. */
+CGEVAP_API int cgevap_adjoint_release(cgevap_sim* sim);
 
 /* ---- ensembles: many independent lattices in one persistent launch ---------------------------
  * An ensemble advances n independent members (D2Q9 and D3Q19 lattices of any sizes, each with its

@@ -26,6 +26,7 @@ _SO = os.path.join(_BUILD, "libcg_oracle.so")
 
 RULE_GRADIENT = 0
 RULE_BAND = 1
+RULE_GIVEN = 2  # replay a recorded site set (bit 0 of ``mask_given``)
 
 
 def build(force: bool = False) -> str:
@@ -54,6 +55,7 @@ class _Params(ctypes.Structure):
         ("phi", ctypes.c_double),
         ("phi_field", ctypes.POINTER(ctypes.c_double)),
         ("solid", ctypes.POINTER(ctypes.c_ubyte)),
+        ("mask_given", ctypes.POINTER(ctypes.c_ubyte)),
     ]
 
 
@@ -123,6 +125,7 @@ class Params:
     phi: float = 0.0
     phi_field: Optional[np.ndarray] = None
     solid: Optional[np.ndarray] = None
+    mask_given: Optional[np.ndarray] = None
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -136,11 +139,12 @@ class Params:
     def _c(self) -> _Params:
         pf = None if self.phi_field is None else np.ascontiguousarray(self.phi_field, np.float64)
         sd = None if self.solid is None else np.ascontiguousarray(self.solid, np.uint8)
-        self._keep = [pf, sd]
+        mg = None if self.mask_given is None else np.ascontiguousarray(self.mask_given, np.uint8)
+        self._keep = [pf, sd, mg]
         return _Params(
             self.q, self.nx, self.ny, self.nz, (ctypes.c_int * 3)(*self.periodic),
             self.rho_r_in, self.rho_b_in, self.tau_r, self.tau_b, self.sigma, self.beta,
-            self.site_rule, self.threshold, self.sbar, self.phi, _dp(pf), _up(sd),
+            self.site_rule, self.threshold, self.sbar, self.phi, _dp(pf), _up(sd), _up(mg),
         )
 
 

@@ -18,7 +18,9 @@
  *   - the perturbation vanishes where |F| = 0;
  *   - f^{b*} = f - f^{r*};
  *   - site rule "band" (|rho^N| < theta on the post-streaming, pre-exchange phase field) is
- *     offered besides the paper's gradient rule; ties are not sites (strict inequalities).
+ *     offered besides the paper's gradient rule; ties are not sites (strict inequalities);
+ *   - site rule "given" replays a recorded site set x_I (one mask per step), so that a
+ *     derivative with respect to phi can be taken with x_I held fixed.
  */
 #include "cg_oracle.h"
 
@@ -154,6 +156,7 @@ static int valid_params(const orc_params *p) {
   if (p->rho_r_in <= 0.0 || p->rho_b_in <= 0.0) return 0;
   if (p->beta < 0.0 || p->beta > 1.0) return 0;
   if (p->sbar <= 0.0) return 0;
+  if (p->site_rule == ORC_RULE_GIVEN && !p->mask_given) return 0;
   return 1;
 }
 
@@ -214,7 +217,11 @@ static int select_and_exchange(const orc_params *p, const lattice *L, double g[2
                                const double *G_prev, long long X, double *margin,
                                double *moved) {
   int site;
-  if (p->site_rule == ORC_RULE_GRADIENT) {
+  if (p->site_rule == ORC_RULE_GIVEN) {
+    /* the site set of an earlier run, replayed: Eq. (exchange) with x_I held fixed */
+    site = p->mask_given[X] & 1;
+    *margin = INFINITY;
+  } else if (p->site_rule == ORC_RULE_GRADIENT) {
     double G = G_prev ? G_prev[X] : 0.0;
     site = G > p->threshold;
     *margin = fabs(G - p->threshold);

@@ -21,6 +21,7 @@ extern "C" {
 
 #define ORC_RULE_GRADIENT 0  /* site if |F| of the previous step > threshold (Sec. II.B)        */
 #define ORC_RULE_BAND     1  /* site if |rho^N| of the current step < threshold (phase band)    */
+#define ORC_RULE_GIVEN    2  /* site where bit 0 of mask_given is set (a replayed site set)     */
 
 typedef struct {
   int q;                 /* 9 (D2Q9, nz must be 1) or 19 (D3Q19)                                */
@@ -30,12 +31,13 @@ typedef struct {
   double tau_r, tau_b;   /* component relaxation times                                          */
   double sigma;          /* surface tension in Eq. (perturb)                                    */
   double beta;           /* recoloring parameter of Eq. (recolor)                               */
-  int site_rule;         /* ORC_RULE_GRADIENT or ORC_RULE_BAND                                  */
+  int site_rule;         /* ORC_RULE_GRADIENT, ORC_RULE_BAND or ORC_RULE_GIVEN                  */
   double threshold;      /* Gamma (gradient rule) or theta (band rule)                          */
   double sbar;           /* S-bar of Eq. (relation)                                             */
   double phi;            /* flux, used when phi_field is NULL                                   */
   const double *phi_field;        /* per-cell flux [z][y][x] or NULL                            */
   const unsigned char *solid;     /* per-cell solid flag [z][y][x] or NULL                      */
+  const unsigned char *mask_given; /* ORC_RULE_GIVEN: sites are the cells whose bit 0 is set     */
 } orc_params;
 
 typedef struct {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcgevap.so")
 F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
 DTYPE_F64, DTYPE_F32 = 0, 1
-SITES_GRADIENT, SITES_BAND = 0, 1
+SITES_GRADIENT, SITES_BAND, SITES_GIVEN = 0, 1, 2
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NAN", -6: "UNSUPPORTED", -7: "IO"}
 
 
@@ -66,6 +66,12 @@ _SIGS = {
     "cgevap_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cgevap_get_macros": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "cgevap_get_mask": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_set_mask": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_volume": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "cgevap_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp]),
+    "cgevap_adjoint_run": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "cgevap_adjoint_release": (ctypes.c_int, [_vp]),
     "cgevap_get_ledger": (ctypes.c_int, [_vp, ctypes.POINTER(Ledger)]),
     "cgevap_reset_ledger": (ctypes.c_int, [_vp]),
     "cgevap_check_health": (ctypes.c_int, [_vp]),
@@ -244,6 +250,40 @@ class Sim:
         self._sync_stream()
         self._check(lib().cgevap_get_mask(self._h, out.data_ptr()))
         return out
+
+    def set_mask(self, mask: torch.Tensor):
+        """Site bytes read by the next step (bit 0 = site under SITES_GIVEN)."""
+        if mask.dtype != torch.uint8 or not mask.is_contiguous() or mask.numel() != self.ncell:
+            raise ValueError("expected a contiguous uint8 tensor of one byte per cell")
+        self._sync_stream()
+        self._check(lib().cgevap_set_mask(self._h, mask.data_ptr()))
+
+    def volume(self) -> torch.Tensor:
+        """Liquid volume sum (1 + rho^N)/2 of the state, FP64, shape [1] (device)."""
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_volume(self._h, out.data_ptr()))
+        return out
+
+    # -- adjoint ----------------------------------------------------------------------------------
+    def adjoint_forward(self, nsteps: int, ckpt_every: int = 64) -> torch.Tensor:
+        """Run nsteps recording checkpoints; returns V(0..nsteps) (FP64, device)."""
+        vol = torch.empty(nsteps + 1, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_adjoint_forward(self._h, int(nsteps), int(ckpt_every), vol.data_ptr()))
+        return vol
+
+    def adjoint_backward(self, dL_dV: Optional[torch.Tensor]) -> torch.Tensor:
+        """dL/dphi per cell (FP64, shape of the lattice) for dL/dV(0..T) of the recorded run."""
+        if dL_dV is not None and (dL_dV.dtype != torch.float64 or not dL_dV.is_contiguous()):
+            raise ValueError("dL_dV must be a contiguous float64 tensor")
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_adjoint_backward(self._h, _ptr(dL_dV), out.data_ptr()))
+        return out
+
+    def adjoint_release(self):
+        self._check(lib().cgevap_adjoint_release(self._h))
 
     def ledger(self) -> dict:
         L = Ledger()

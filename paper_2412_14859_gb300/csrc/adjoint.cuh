@@ -1,0 +1,380 @@
+// adjoint.cuh -- reverse-mode derivative of one fused step with respect to its input state and
+// the flux field, with the site set x_I of the step held fixed.
+//
+// The step maps the stored state f^n to f^{n+1}: for every fluid cell x
+//   g(x)    = pulled populations (Eq. Stream, halfway bounce-back), then Eq. (exchange):
+//             g_0^r -= m(x) phi(x)/S-bar, g_0^b += m(x) phi(x)/S-bar;
+//   F(x)    = 3 sum_i W_i c_i rho^N(n_i(x)),  n_i(x) = x + c_i, or x where x + c_i is solid or
+//             beyond a wall (Eq. cg), rho^N = (rho_r - rho_b)/rho of the post-exchange g;
+//   f^{n+1}(x) = C(g(x), F(x)): Eq. (feq), (collision), (perturb), (recolor).
+// Given lambda^{n+1} = dL/df^{n+1} and w = dL/dV(n+1) for the observable
+// V(n+1) = sum_x (1 + rho^N(x))/2 (the stored densities of f^{n+1} are those of g: the
+// collision, the perturbation and the recoloring conserve rho_r and rho_b per cell), the sweep is
+//   (1) local:   lg(x) = (dC/dg)^T lambda^{n+1}(x),  lF(x) = (dC/dF)^T lambda^{n+1}(x),
+//                plus d rho^N/d(rho_r, rho_b) = (2 rho_b, -2 rho_r)/rho^2          [kernel A]
+//   (2) stencil: mu(y) = w/2 + sum_{(x,i): n_i(x) = y} 3 W_i c_i . lF(x);
+//                lg_total(y) = lg(y) + mu(y) d rho^N/d(rho_r, rho_b) on every direction;
+//                dL/dphi(y) += m(y) (lg_total_0^b(y) - lg_total_0^r(y)) / S-bar     [kernel B1]
+//   (3) pull^T:  lambda^n_j(y) = lg_total_j(y + c_j), or lg_total_{opp j}(y) where y + c_j is
+//                solid or beyond a wall (the transpose of the pull with bounce-back)  [kernel B2]
+// Kernel A recomputes the forward quantities of its tile exactly as the step does (it runs the
+// step's own tile code with this file's epilogue in place of the collision/store).
+#pragma once
+
+#include "launch.h"
+#include "step_kernel.cuh"
+
+namespace cgevap {
+
+// Pull source of direction i from the cell with slot sl at storage index si (see pull_cell).
+template <class L>
+__device__ __forceinline__ int pull_source(const Slot& sl, const PlaneOffsets& po, int si, int i) {
+  return si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+         (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+         (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+}
+
+// (1) for one cell: recompute the moments, F and the per-direction terms of collide_store and
+// run them backwards.  g: post-exchange populations; lam: dL/d(f^{r*}, f^{b*}) of this cell;
+// out: lg = dL/dg through this cell's own collision, lF = dL/dF.
+template <int Q, class R>
+__device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (&g)[Q], R rr, R rb,
+                                                R irho, const R (&rnb)[Q], const V2<R> (&lam)[Q],
+                                                V2<R> (&lg)[Q], R (&lF)[3]) {
+  using L = Lattice<Q>;
+  const R rho = rr + rb;
+  const R wr = rr * irho, wb = rb * irho;
+  R f[Q];
+  R ja = R(0), jb = R(0), jm = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    f[i] = g[i].r + g[i].b;
+    if (L::ca(i) > 0) ja += f[i];
+    if (L::ca(i) < 0) ja -= f[i];
+    if (L::cb(i) > 0) jb += f[i];
+    if (L::cb(i) < 0) jb -= f[i];
+    if (L::cm(i) > 0) jm += f[i];
+    if (L::cm(i) < 0) jm -= f[i];
+  }
+  const R ua = ja * irho, ub = jb * irho, um = jm * irho;
+  const R uu15 = R(1.5) * (ua * ua + ub * ub + um * um);
+  const R ir = (R)ph.inv_tau_r, ib = (R)ph.inv_tau_b;
+  const R itau = wr * ir + wb * ib;
+  const R abar = wr * (R)ph.alpha_r + wb * (R)ph.alpha_b;
+  R Fa = R(0), Fb = R(0), Fm = R(0);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const R t = R(3.0 * L::W(i)) * rnb[i];
+    if (L::ca(i) > 0) Fa += t;
+    if (L::ca(i) < 0) Fa -= t;
+    if (L::cb(i) > 0) Fb += t;
+    if (L::cb(i) < 0) Fb -= t;
+    if (L::cm(i) > 0) Fm += t;
+    if (L::cm(i) < 0) Fm -= t;
+  }
+  const R F2 = Fa * Fa + Fb * Fb + Fm * Fm;
+  R Fn = R(0), iFn = R(0);
+  if (F2 > R(0)) norm_pair<R>(F2, Fn, iFn);
+  const R amp = (R)ph.amp, beta = (R)ph.beta;
+  const R pamp = amp * itau;
+  const R rcol = beta * wr * wb;
+  R restc[3], rwc[3], kw[3], kc[3], kr[3], nrm[3], As[3], Bs[3], Ws[3], Cs[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = c == 0 ? 0 : (c == 1 ? 1 : L::Q - 1);
+    As[c] = R(L::A(i));
+    Bs[c] = R(L::B(i));
+    Ws[c] = R(L::W(i));
+    Cs[c] = R(L::C(i));
+    nrm[c] = R(inv_norm<L>(i));
+    restc[c] = rho * (As[c] + Bs[c] * abar);
+    rwc[c] = rho * Ws[c];
+    kw[c] = pamp * Ws[c] * iFn;
+    kc[c] = pamp * Cs[c] * Fn;
+    kr[c] = rcol * iFn * nrm[c] * restc[c];
+  }
+
+  // Backwards through recolor -> perturb -> collision -> feq, direction by direction.
+  R A_wr = R(0), A_itau = R(0), A_uu15 = R(0);
+  R A_kr[3] = {R(0), R(0), R(0)}, A_kw[3] = {R(0), R(0), R(0)}, A_kc[3] = {R(0), R(0), R(0)};
+  R A_rwc[3] = {R(0), R(0), R(0)}, A_restc[3] = {R(0), R(0), R(0)};
+  R Aua = R(0), Aub = R(0), Aum = R(0), AFa = R(0), AFb = R(0), AFm = R(0);
+  R Af[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int c = L::speed2(i);
+    R cu = R(0), pc = R(0);
+    if (L::ca(i) > 0) { cu += ua; pc += Fa; }
+    if (L::ca(i) < 0) { cu -= ua; pc -= Fa; }
+    if (L::cb(i) > 0) { cu += ub; pc += Fb; }
+    if (L::cb(i) < 0) { cu -= ub; pc -= Fb; }
+    if (L::cm(i) > 0) { cu += um; pc += Fm; }
+    if (L::cm(i) < 0) { cu -= um; pc -= Fm; }
+    const R poly = cu * (R(4.5) * cu + R(3)) - uu15;
+    const R feq = rwc[c] * poly + restc[c];
+    const R fi = f[i] + itau * (feq - f[i]) + kw[c] * pc * pc - kc[c];  // post-perturbation
+    // Eq. (recolor): f^{r*} = wr fi + kr pc, f^{b*} = fi - f^{r*}
+    const R d = lam[i].r - lam[i].b;
+    const R q = wr * d + lam[i].b;  // dL/dfi
+    A_wr += d * fi;
+    A_kr[c] += d * pc;
+    // Eq. (perturb): fi += kw pc^2 - kc
+    const R A_pc = d * kr[c] + R(2) * q * kw[c] * pc;
+    A_kw[c] += q * pc * pc;
+    A_kc[c] -= q;
+    // Eq. (collision): fi = f + itau (feq - f)
+    const R A_feq = q * itau;
+    Af[i] = q * (R(1) - itau);
+    A_itau += q * (feq - f[i]);
+    // Eq. (feq): feq = rwc (cu (9/2 cu + 3) - 3/2 u^2) + restc
+    A_rwc[c] += A_feq * poly;
+    A_restc[c] += A_feq;
+    const R A_cu = A_feq * rwc[c] * (R(9) * cu + R(3));
+    A_uu15 -= A_feq * rwc[c];
+    if (L::ca(i) > 0) { Aua += A_cu; AFa += A_pc; }
+    if (L::ca(i) < 0) { Aua -= A_cu; AFa -= A_pc; }
+    if (L::cb(i) > 0) { Aub += A_cu; AFb += A_pc; }
+    if (L::cb(i) < 0) { Aub -= A_cu; AFb -= A_pc; }
+    if (L::cm(i) > 0) { Aum += A_cu; AFm += A_pc; }
+    if (L::cm(i) < 0) { Aum -= A_cu; AFm -= A_pc; }
+  }
+  // Speed-class factors: kr = rcol iFn nrm restc, kw = pamp W iFn, kc = pamp C |F|,
+  // restc = rho (A + B abar), rwc = rho W.
+  R A_rcol = R(0), A_iFn = R(0), A_Fn = R(0), A_pamp = R(0), A_rho = R(0), A_abar = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    A_rcol += A_kr[c] * iFn * nrm[c] * restc[c];
+    A_iFn += A_kr[c] * rcol * nrm[c] * restc[c] + A_kw[c] * pamp * Ws[c];
+    const R A_rc = A_restc[c] + A_kr[c] * rcol * iFn * nrm[c];
+    A_pamp += A_kw[c] * Ws[c] * iFn + A_kc[c] * Cs[c] * Fn;
+    A_Fn += A_kc[c] * pamp * Cs[c];
+    A_rho += A_rc * (As[c] + Bs[c] * abar) + A_rwc[c] * Ws[c];
+    A_abar += A_rc * rho * Bs[c];
+  }
+  A_itau += A_pamp * amp;
+  R A_wb = R(0);
+  A_wr += A_rcol * beta * wb + A_itau * ir + A_abar * (R)ph.alpha_r;
+  A_wb += A_rcol * beta * wr + A_itau * ib + A_abar * (R)ph.alpha_b;
+  // u = j / rho, uu15 = 3/2 |u|^2
+  Aua += R(3) * A_uu15 * ua;
+  Aub += R(3) * A_uu15 * ub;
+  Aum += R(3) * A_uu15 * um;
+  A_rho -= (Aua * ua + Aub * ub + Aum * um) * irho;
+  const R Aja = Aua * irho, Ajb = Aub * irho, Ajm = Aum * irho;
+  // |F| and 1/|F| as functions of F (zero where F = 0, as in the step)
+  if (F2 > R(0)) {
+    const R s = (A_Fn - A_iFn * iFn * iFn) * iFn;
+    AFa += s * Fa;
+    AFb += s * Fb;
+    AFm += s * Fm;
+  }
+  lF[0] = AFa;
+  lF[1] = AFb;
+  lF[2] = AFm;
+  // wr = rr / rho, wb = rb / rho, rho = rr + rb
+  const R A_rr = A_rho + (A_wr - A_wb) * wb * irho;
+  const R A_rb = A_rho + (A_wb - A_wr) * wr * irho;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R a = Af[i];
+    if (L::ca(i) > 0) a += Aja;
+    if (L::ca(i) < 0) a -= Aja;
+    if (L::cb(i) > 0) a += Ajb;
+    if (L::cb(i) < 0) a -= Ajb;
+    if (L::cm(i) > 0) a += Ajm;
+    if (L::cm(i) < 0) a -= Ajm;
+    lg[i] = {a + A_rr, a + A_rb};
+  }
+}
+
+// Kernel A's per-cell tail (replaces StepEpilogue in step_tile): reads lambda^{n+1} at the cell,
+// writes lg (state layout) and the auxiliary planes.
+struct AdjointEpilogue {
+  AdjointOut o;
+  template <int Q, int S, class R>
+  __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, int si, int /*nimg*/,
+                                       const int (&)[3], const V2<R> (&g)[Q], R rr, R rb, R irho,
+                                       R /*e*/, uint32_t /*flags*/, const R (&rnb)[Q],
+                                       long long&, double&) const {
+    using Vec = typename Storage<S>::vec;
+    const int ns = A.g.nstore;
+    const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);
+    V2<R> lam[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const Vec v = __ldg(lin + (size_t)i * ns + si);
+      lam[i] = {v.x, v.y};
+    }
+    V2<R> lg[Q];
+    R lF[3];
+    collide_adjoint<Q, R>(A.ph, g, rr, rb, irho, rnb, lam, lg, lF);
+    Vec* lout = reinterpret_cast<Vec*>(o.lam_g);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      Vec v;
+      v.x = lg[i].r;
+      v.y = lg[i].b;
+      lout[(size_t)i * ns + si] = v;
+    }
+    R* ax = reinterpret_cast<R*>(o.aux);
+    ax[si] = lF[0];
+    ax[(size_t)ns + si] = lF[1];
+    ax[2 * (size_t)ns + si] = lF[2];
+    ax[3 * (size_t)ns + si] = R(2) * rb * irho * irho;   // d rho^N / d rho_r
+    ax[4 * (size_t)ns + si] = -R(2) * rr * irho * irho;  // d rho^N / d rho_b
+  }
+};
+
+template <int Q, int S, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, 1)
+    cg_adjoint_local_kernel(const __grid_constant__ StepArgs A,
+                            const __grid_constant__ AdjointOut O) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  long long n = 0;
+  double d = 0.0;
+  const AdjointEpilogue E{O};
+  step_tile<Q, S, TX, TY, 1, AdjointEpilogue>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d,
+                                              threadIdx.x, -1, E);
+}
+
+__device__ __forceinline__ void cell_coords(const Geom& g, int cell, int& a, int& b, int& m) {
+  a = cell % g.na;
+  const int t = cell / g.na;
+  b = t % g.nb;
+  m = t / g.nb;
+}
+
+// (2) one thread per cell.  dLdV: pointer to dL/dV(n+1) (nullptr: 0).
+template <int Q, class R>
+__global__ void __launch_bounds__(256)
+    cg_adjoint_stencil_kernel(Geom G, const R* __restrict__ aux, const void* __restrict__ lam_g,
+                              void* __restrict__ ab, const uint8_t* __restrict__ mask,
+                              double* __restrict__ dphi, double inv_sbar,
+                              const double* __restrict__ dLdV) {
+  using L = Lattice<Q>;
+  using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= G.ncell) return;
+  int a, b, m;
+  cell_coords(G, cell, a, b, m);
+  const Slot sl = make_slot<L>(G, a, b);
+  const Plane p = make_plane(G, m);
+  uint32_t bits = 0;
+  if (!solid_bits<L>(G, sl, p, cell, bits)) return;
+  const PlaneOffsets po = plane_offsets(G, m);
+  const int si = sidx(G, a, b, m);
+  const size_t ns = G.nstore;
+  const R oa = aux[si], ob = aux[ns + si], om = aux[2 * ns + si];
+  R mu = dLdV ? R(0.5 * __ldg(dLdV)) : R(0);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    R t = R(0);
+    if (!((bits >> i) & 1u)) {  // x = y - c_i is fluid: its F used rho^N(y) with weight 3 W_i c_i
+      const int src = pull_source<L>(sl, po, si, i);
+      if (L::ca(i)) t += R(L::ca(i)) * __ldg(aux + src);
+      if (L::cb(i)) t += R(L::cb(i)) * __ldg(aux + ns + src);
+      if (L::cm(i)) t += R(L::cm(i)) * __ldg(aux + 2 * ns + src);
+    }
+    if ((bits >> opp(i)) & 1u)  // y + c_i is solid: y's own F used rho^N(y) in its place
+      t += R(L::ca(i)) * oa + R(L::cb(i)) * ob + R(L::cm(i)) * om;
+    mu += R(3.0 * L::W(i)) * t;
+  }
+  Vec v;
+  v.x = mu * aux[3 * ns + si];
+  v.y = mu * aux[4 * ns + si];
+  reinterpret_cast<Vec*>(ab)[si] = v;
+  if (mask[cell] & 1u) {  // Eq. (exchange): d g_0^r / d phi = -1/S-bar, d g_0^b / d phi = +1/S-bar
+    const Vec l0 = reinterpret_cast<const Vec*>(lam_g)[si];
+    dphi[cell] += ((double)(l0.y + v.y) - (double)(l0.x + v.x)) * inv_sbar;
+  }
+}
+
+// (3) one thread per cell: the pull transposed.
+template <int Q, class R>
+__global__ void __launch_bounds__(256)
+    cg_adjoint_gather_kernel(Geom G, const void* __restrict__ lam_g, const void* __restrict__ ab,
+                             void* __restrict__ lam_out) {
+  using L = Lattice<Q>;
+  using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= G.ncell) return;
+  int a, b, m;
+  cell_coords(G, cell, a, b, m);
+  const Slot sl = make_slot<L>(G, a, b);
+  const Plane p = make_plane(G, m);
+  uint32_t bits = 0;
+  if (!solid_bits<L>(G, sl, p, cell, bits)) return;
+  const PlaneOffsets po = plane_offsets(G, m);
+  const int si = sidx(G, a, b, m);
+  const size_t ns = G.nstore;
+  const Vec* lg = reinterpret_cast<const Vec*>(lam_g);
+  const Vec* abv = reinterpret_cast<const Vec*>(ab);
+  Vec* out = reinterpret_cast<Vec*>(lam_out);
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    int src = si, dir = j;
+    if (j != 0) {
+      if ((bits >> opp(j)) & 1u) dir = opp(j);          // y + c_j solid: bounce-back link
+      else src = pull_source<L>(sl, po, si, opp(j));     // y + c_j
+    }
+    const Vec l = __ldg(lg + (size_t)dir * ns + src);
+    const Vec w = __ldg(abv + src);
+    Vec v;
+    v.x = l.x + w.x;
+    v.y = l.y + w.y;
+    out[(size_t)j * ns + si] = v;
+  }
+}
+
+// V = sum over fluid cells of (1 + rho^N)/2 of a stored state, FP64, deterministic: fixed grid,
+// per-block partials, the last block to arrive adds them in block order into *out.
+template <int Q, int S>
+__global__ void __launch_bounds__(256)
+    cg_volume_kernel(Geom G, Physics ph, const void* __restrict__ state, double* __restrict__ part,
+                     unsigned int* __restrict__ done, double* __restrict__ out) {
+  using R = typename Storage<S>::real;
+  __shared__ double red[8];
+  __shared__ int is_last;
+  double v = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < G.ncell; cell += stride) {
+    if (G.links && (__ldg(G.links + cell) >> 31)) continue;
+    int a, b, m;
+    cell_coords(G, cell, a, b, m);
+    const int si = sidx(G, a, b, m);
+    R rr = R(0), rb = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const V2<R> f = PopIO<S, Q>::load(state, G.nstore, i, i, si, ph);
+      rr += f.r;
+      rb += f.b;
+    }
+    v += 0.5 * (1.0 + ((double)rr - (double)rb) / ((double)rr + (double)rb));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int tid = threadIdx.x;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
+    __threadfence();
+    is_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last && tid < 32) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned j = tid; j < gridDim.x; j += 32) s += __ldcg(part + j);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (tid == 0) {
+      *out = s;
+      *done = 0u;
+    }
+  }
+}
+
+}  // namespace cgevap

@@ -8,52 +8,16 @@
 #include <string>
 #include <vector>
 
-#include "../../include/cgevap.h"
-#include "launch.h"
+#include "sim.h"
 
 using namespace cgevap;
 
-struct cgevap_sim {
-  cgevap_params p;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int Q = 0;
-  long long N = 0;
-  long long nfluid = 0;
-  Geom geom{};
-  Physics ph{};
-  size_t state_bytes = 0;
-  void* state[2] = {nullptr, nullptr};
-  uint8_t* mask[2] = {nullptr, nullptr};
-  int cur = 0;
-  uint32_t* links = nullptr;
-  uint8_t* solid = nullptr;
-  void* phi_field = nullptr;  // double (F64 storage) or float, [N]
-  double phi = 0.0;
-  DevLedger* ledger = nullptr;
-  double* part_removed = nullptr;
-  long long* part_sites = nullptr;
-  unsigned int* done = nullptr;
-  long long part_capacity = 0;
-  double* tmp_rn = nullptr;
-  int* flag = nullptr;
-  int* status = nullptr;  // set by a bounded device-side wait that gave up
-  void* staging = nullptr;  // device staging for host imports
-  size_t staging_bytes = 0;
-  // launch plan of the fused step
-  int family = 0;  // 0 register-pipelined kernel, 1 TMA-pipelined kernel
-  int variant = 0;
-  KernelRef kernel{nullptr, 0};
-  alignas(64) unsigned char tmap[2][128];  // TMA tensor maps of state[0] and state[1]
-  int ntx = 1, nty = 1, pc = 1, nchunk = 1;
-  std::string err;
-};
 
 namespace {
-
 thread_local std::string g_create_error;
+}  // namespace
 
-int fail(cgevap_sim* s, int code, const std::string& msg) {
+int cgevap::sim_fail(cgevap_sim* s, int code, const std::string& msg) {
   if (s)
     s->err = msg;
   else
@@ -61,12 +25,10 @@ int fail(cgevap_sim* s, int code, const std::string& msg) {
   return code;
 }
 
-#define CG_CUDA(s, call)                                                                 \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail((s), CGEVAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
+namespace {
+
+int fail(cgevap_sim* s, int code, const std::string& msg) { return sim_fail(s, code, msg); }
+
 
 double w0_of(int q) { return q == 19 ? Lattice<19>::W(0) : Lattice<9>::W(0); }
 
@@ -83,7 +45,8 @@ std::string validate(const cgevap_params* p) {
   if (!(p->beta >= 0.0 && p->beta <= 1.0)) return "beta must lie in [0, 1]";
   if (!(p->sbar > 0.0)) return "sbar must be > 0";
   if (!std::isfinite(p->sigma) || !std::isfinite(p->threshold)) return "sigma/threshold not finite";
-  if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND)
+  if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND &&
+      p->site_rule != CGEVAP_SITES_GIVEN)
     return "unknown site rule";
   if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16DEV) return "unknown storage";
   return "";
@@ -134,7 +97,9 @@ void setup_physics(cgevap_sim* s) {
   ph.inv_scale = 1.0f / ph.scale;
 }
 
-AuxArgs aux_of(const cgevap_sim* s) {
+}  // namespace
+
+AuxArgs cgevap::aux_of(const cgevap_sim* s) {
   AuxArgs a;
   a.g = s->geom;
   a.ph = s->ph;
@@ -144,6 +109,8 @@ AuxArgs aux_of(const cgevap_sim* s) {
   a.rho_b_in = s->p.rho_b_in;
   return a;
 }
+
+namespace {
 
 KernelRef kernel_for(int q, int storage, int variant) {
   switch (storage) {
@@ -227,7 +194,9 @@ int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
   return CGEVAP_OK;
 }
 
-int launch_one_step(cgevap_sim* s) {
+}  // namespace
+
+StepArgs cgevap::step_args(cgevap_sim* s) {
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.g = s->geom;
@@ -244,6 +213,13 @@ int launch_one_step(cgevap_sim* s) {
   a.pout = s->state[s->cur ^ 1];
   a.mask_in = s->mask[s->cur];
   a.mask_out = s->mask[s->cur ^ 1];
+  return a;
+}
+
+namespace {
+
+int launch_one_step(cgevap_sim* s) {
+  StepArgs a = step_args(s);
   void* args[] = {&a, s->tmap[s->cur]};
   CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
                               dim3(s->kernel.threads), args, s->kernel.smem, s->stream));
@@ -264,9 +240,11 @@ int refresh_gradient_sites(cgevap_sim* s) {
 
 void release(cgevap_sim* s) {
   if (!s) return;
+  adjoint_release(s);
   void* ptrs[] = {s->state[0], s->state[1], s->mask[0],  s->mask[1],  s->links,
                   s->solid,    s->phi_field, s->ledger, s->part_removed, s->part_sites,
-                  s->done,     s->tmp_rn,   s->flag,    s->staging, s->status};
+                  s->done,     s->tmp_rn,   s->flag,    s->staging, s->status,
+                  s->vol_part, s->vol_done};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete s;
@@ -539,6 +517,13 @@ int cgevap_get_mask(cgevap_sim* s, uint8_t* dev_mask) {
   return CGEVAP_OK;
 }
 
+int cgevap_set_mask(cgevap_sim* s, const uint8_t* dev_mask) {
+  if (!s || !dev_mask) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, cudaMemcpyAsync(s->mask[s->cur], dev_mask, s->N, cudaMemcpyDeviceToDevice, s->stream));
+  return CGEVAP_OK;
+}
+
 int cgevap_get_ledger(cgevap_sim* s, cgevap_ledger* out) {
   if (!s || !out) return CGEVAP_ERR_ARG;
   CG_CUDA(s, cudaSetDevice(s->device));
@@ -716,7 +701,7 @@ double cgevap_bytes_per_update(const cgevap_sim* s) {
     case CGEVAP_F32: pops = 2.0 * 2 * Q * 4; break;
     default: pops = 2.0 * (8 + (Q - 1) * 4); break;
   }
-  const double mask = s->p.site_rule == CGEVAP_SITES_GRADIENT ? 2.0 : 1.0;
+  const double mask = s->p.site_rule == CGEVAP_SITES_BAND ? 1.0 : 2.0;  // read + write
   const double field = s->ph.phi_field ? (s->p.storage == CGEVAP_F64 ? 8.0 : 4.0) : 0.0;
   return pops + mask + field;
 }

@@ -67,4 +67,28 @@ cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s);
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s);
 
+// Adjoint sweep (adjoint_kernels.cu).  The local kernel (kernel A) takes (StepArgs, AdjointOut)
+// and runs on the step's tile grid; F64 / F32 storage only.
+// Auxiliary per-cell fields of the sweep, planes of nstore reals in the storage layout:
+// dL/dF_a, dL/dF_b, dL/dF_m, d rho^N/d rho_r, d rho^N/d rho_b.
+constexpr int kAdjAuxPlanes = 5;
+struct AdjointOut {
+  const void* lam_in;  // lambda^{n+1} = dL/df^{n+1}, state layout (vec2 per direction, index)
+  void* lam_g;         // out: dL/dg through each cell's own collision, state layout
+  void* aux;           // out: kAdjAuxPlanes planes
+};
+KernelRef adjoint_local_kernel(int q, int storage);
+// Kernel B1: stencil transpose, exchange derivative into dphi (FP64, compact [N]); aux holds
+// kAdjAuxPlanes planes of nstore reals; ab receives nstore vec2.  dLdV may be nullptr.
+cudaError_t launch_adjoint_stencil(const AuxArgs& a, const void* aux, const void* lam_g, void* ab,
+                                   const uint8_t* mask, double* dphi, double inv_sbar,
+                                   const double* dLdV, cudaStream_t s);
+// Kernel B2: the pull transposed, lam_out = lambda^n in the state layout.
+cudaError_t launch_adjoint_gather(const AuxArgs& a, const void* lam_g, const void* ab,
+                                  void* lam_out, cudaStream_t s);
+// Liquid volume of a state into *out (FP64); part holds kVolumeBlocks doubles, *done starts at 0.
+constexpr int kVolumeBlocks = 608;
+cudaError_t launch_volume(const AuxArgs& a, const void* state, double* part, unsigned int* done,
+                          double* out, cudaStream_t s);
+
 }  // namespace cgevap

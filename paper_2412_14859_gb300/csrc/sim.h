@@ -1,0 +1,68 @@
+// sim.h -- the simulation handle behind include/cgevap.h and the library-internal helpers that
+// the entry points in api.cu and adjoint.cu share.  Not installed, not part of the ABI.
+#pragma once
+
+#include <string>
+
+#include "../../include/cgevap.h"
+#include "launch.h"
+
+namespace cgevap {
+struct AdjointTape;
+}
+
+struct cgevap_sim {
+  cgevap_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int Q = 0;
+  long long N = 0;
+  long long nfluid = 0;
+  cgevap::Geom geom{};
+  cgevap::Physics ph{};
+  size_t state_bytes = 0;
+  void* state[2] = {nullptr, nullptr};
+  uint8_t* mask[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t* links = nullptr;
+  uint8_t* solid = nullptr;
+  void* phi_field = nullptr;  // double (F64 storage) or float, [N]
+  double phi = 0.0;
+  cgevap::DevLedger* ledger = nullptr;
+  double* part_removed = nullptr;
+  long long* part_sites = nullptr;
+  unsigned int* done = nullptr;
+  long long part_capacity = 0;
+  double* tmp_rn = nullptr;
+  int* flag = nullptr;
+  int* status = nullptr;  // set by a bounded device-side wait that gave up
+  void* staging = nullptr;  // device staging for host imports
+  size_t staging_bytes = 0;
+  // launch plan of the fused step
+  int family = 0;  // 0 register-pipelined kernel, 1 TMA-pipelined kernel
+  int variant = 0;
+  cgevap::KernelRef kernel{nullptr, 0};
+  alignas(64) unsigned char tmap[2][128];  // TMA tensor maps of state[0] and state[1]
+  int ntx = 1, nty = 1, pc = 1, nchunk = 1;
+  cgevap::AdjointTape* tape = nullptr;  // checkpoints of cgevap_adjoint_forward (adjoint.cu)
+  double* vol_part = nullptr;           // cgevap_volume scratch: kVolumeBlocks partials
+  unsigned int* vol_done = nullptr;     // and its arrival counter
+  std::string err;
+};
+
+namespace cgevap {
+// Records msg as the handle's last error (or the create error) and returns code.
+int sim_fail(cgevap_sim* s, int code, const std::string& msg);
+AuxArgs aux_of(const cgevap_sim* s);
+// Arguments of one fused step of the current plan, reading state[cur] and writing state[cur^1].
+StepArgs step_args(cgevap_sim* s);
+// Adjoint tape release (adjoint.cu), called when the handle is destroyed.
+void adjoint_release(cgevap_sim* s);
+}  // namespace cgevap
+
+#define CG_CUDA(s, call)                                                                          \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return ::cgevap::sim_fail((s), CGEVAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)

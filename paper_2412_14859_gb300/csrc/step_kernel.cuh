@@ -150,9 +150,11 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
     site = d < R(0);
     near = fabs(d) < R(1e-6);
   } else {
+    // gradient rule: the decision of the previous step (bit 1); given rule: bit 0
     const uint32_t mb = A.mask_in[cell];
-    site = (mb >> 1) & 1u;
-    near = (mb >> 3) & 1u;
+    const int sh = A.ph.rule == 2 ? 0 : 1;
+    site = (mb >> sh) & 1u;
+    near = (mb >> (sh + 2)) & 1u;
   }
   e = site ? flux_at<S>(A.ph, cell) : R(0);
   g[0].r -= e;
@@ -359,6 +361,30 @@ __device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d
   return n;
 }
 
+// Per-cell tail of the fused step, called by step_tile for every fluid cell of the tile once its
+// pulled, post-exchange populations g and the neighbour phase field rnb are at hand: Eq.
+// (collision) to Eq. (recolor) and the store, the site byte of this step and the ledger terms.
+struct StepEpilogue {
+  template <int Q, int S, class R>
+  __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
+                                       const int (&dimg)[3], const V2<R> (&g)[Q], R rr, R rb,
+                                       R irho, R e, uint32_t flags, const R (&rnb)[Q],
+                                       long long& n_sites, double& removed) const {
+    R Fn;
+    collide_store<Q, S>(A, si, nimg, dimg, g, rr, rb, irho, rnb, Fn);
+    uint32_t mb = flags;
+    if (A.ph.rule == 0) {
+      const R d = Fn - (R)A.ph.threshold;
+      mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
+    }
+    A.mask_out[cell] = (uint8_t)mb;
+    if (flags & 1u) {
+      ++n_sites;
+      removed += (double)e;
+    }
+  }
+};
+
 // Shared-memory footprint of step_tile: the rho^N ring, the deviation storages' rest ring and
 // the parking columns (bytes).
 template <int Q, int S, int TX, int TY, int CPT>
@@ -383,11 +409,13 @@ struct TileSmem {
 // TileSmem<...>::BYTES bytes of shared memory.  Returns this thread's site count and removed mass.
 // tid: this thread's index within the TX*TY threads that run the tile; iters >= the number of
 // planes of the chunk: the loop runs that many barrier rounds (the extra ones idle), so several
-// tiles with different chunk lengths can share one CTA's barriers.
-template <int Q, int S, int TX, int TY, int CPT>
+// tiles with different chunk lengths can share one CTA's barriers.  epi: the per-cell tail
+// (StepEpilogue for the step itself; the adjoint passes its own).
+template <int Q, int S, int TX, int TY, int CPT, class Epi = StepEpilogue>
 __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk, unsigned char* smem,
                                           long long& n_sites, double& removed,
-                                          int tid = threadIdx.x, int iters = -1) {
+                                          int tid = threadIdx.x, int iters = -1,
+                                          const Epi& epi = Epi()) {
   using SM = TileSmem<Q, S, TX, TY, CPT>;
   unsigned char* ring_mem = smem;
   unsigned char* rest_mem = smem + SM::RING;
@@ -621,19 +649,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         rnb[i] = solid_nb ? ownrn : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
-      R Fn;
-      collide_store<Q, S>(A, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own, cur[c].rr,
-                          cur[c].rb, cur[c].irho, rnb, Fn);
-      uint32_t mb = cur[c].flags;
-      if (A.ph.rule == 0) {
-        const R d = Fn - (R)A.ph.threshold;
-        mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
-      }
-      A.mask_out[cell] = (uint8_t)mb;
-      if (cur[c].flags & 1u) {
-        ++n_sites;
-        removed += (double)cur[c].e;
-      }
+      epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
+                              cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
+                              n_sites, removed);
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];

@@ -172,9 +172,15 @@ def sphere_3d(n: int = 192, R0: float = 32.0) -> Case:
 
 def sessile_cap_3d(shape=(128, 256, 256), R0: float = 48.0, phi0: float = 2e-5) -> Case:
     """D3Q19 90-degree cap of radius R0 on the bounce-back wall z = -1/2 of a box with walls at
-    both ends of z, unit density ratio, A = 0.01, band threshold 0.5, FP32, 2000 steps."""
+    both ends of z, unit density ratio, A = 0.005, band threshold 0.5, FP32, 2000 steps."""
     return Case("sessile_cap_3d", 19, tuple(shape), periodic=(1, 1, 0), R0=R0, phi=phi0,
                 geometry="cap", steps=2000, sigma=sigma_from_amplitude(0.005))
+
+
+def flux_fit_parameters(K: int = 16, seed: int = SEED):
+    """Coefficients of the flux polynomial: a ~ N(0, 0.1) (seed) and the target set a_target ~
+    N(0, 0.1) (seed + 1), K each."""
+    return (rng(seed).normal(0.0, 0.1, K), rng(seed + 1).normal(0.0, 0.1, K))
 
 
 def ensemble_members(seed: int = SEED) -> List[Case]:

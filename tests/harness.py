@@ -45,6 +45,32 @@ def gpu_sim(case: inputs.Case, storage: str, phi_field=None, solid=None, kernel=
     return sim
 
 
+def adjoint_case(q):
+    """Small lattice with sites, walls and (3D) one solid cell, a seeded flux field and a noisy
+    initial state: (oracle params, f0, phi field)."""
+    if q == 9:  # D2Q9 drop touching nothing, walls across y
+        shape = (1, 14, 17)
+        per = (1, 0, 1)
+        phase = inputs.sphere_phase(shape, (0.0, 6.5, 8.0), 4.5)
+    else:       # D3Q19 cap on the z = -1/2 wall, walls at both ends of z, one solid cell
+        shape = (8, 9, 10)
+        per = (1, 1, 0)
+        phase = inputs.sphere_phase(shape, (-0.5, 4.0, 4.5), 4.2)
+    solid = None
+    if q == 19:
+        solid = np.zeros(shape, np.uint8)
+        solid[5, 1, 1] = 1
+    phi = 2e-3 * (1.0 + inputs.uniform_noise(shape, 0.3, seed=inputs.SEED + 7))
+    nz, ny, nx = shape
+    p = oracle.Params(q, nx, ny, nz, per, rho_r_in=1.0, rho_b_in=1.0, tau_r=1.0, tau_b=0.8,
+                      sigma=inputs.sigma_from_amplitude(0.01), beta=0.7,
+                      site_rule=oracle.RULE_BAND, threshold=0.5, sbar=3.0, phi_field=phi,
+                      solid=solid)
+    noise = inputs.uniform_noise((2, q) + shape, 1e-6)
+    f0 = oracle.init(p, phase, noise)
+    return p, f0, phi
+
+
 def rel_linf(a, b) -> float:
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
