@@ -12,6 +12,12 @@ speed and their error against the FP64 path.
 
 N > 1 runs under torchrun as N independent replicas (weak scaling, no data-path collective).
 `--impl reference` times the FP64 CPU oracle (the only reference this paper has) on the host.
+
+The line also carries the 64-member ensemble (one persistent launch per graph replay) and one
+iteration of the adjoint flux fit: a D3Q19 90-degree sessile cap R0 = 48 on a wall of a
+256x256x128 box, FP32, 2000 steps with checkpoints every 64, the 16 coefficients of
+phi = phi0 (1 + sum_k a_k (r/R)^k) differentiated through the hand-written reverse sweep.
+`--adjoint-fd` instead prints the agreement of that gradient with central finite differences.
 """
 from __future__ import annotations
 
@@ -46,6 +52,12 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel", type=int, default=-1, help="-1 auto, 0 register, 1 TMA pipeline")
     ap.add_argument("--variant", type=int, default=0, help="tile / pipeline variant of the kernel")
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="steps of the adjoint flux-fit iteration (0: skip)")
+    ap.add_argument("--adjoint-shape", default="128,256,256",
+                    help="nz,ny,nx of the sessile cap (R0 = 48 nx / 256)")
+    ap.add_argument("--adjoint-fd", action="store_true",
+                    help="only check the flux-fit gradient against finite differences (FP64)")
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="steps of the 64-member ensemble workload (0: skip)")
     return ap.parse_args()
@@ -284,6 +296,143 @@ def run_ensemble(args, dev):
     return out
 
 
+def cap_fit(shape, R0, dev, dtype):
+    """Sessile-cap flux-fit problem: case, radial basis (r/R0)^k, a, a_target."""
+    import torch
+    from paper_2412_14859_gb300 import inputs
+    case = inputs.sessile_cap_3d(shape, R0=R0, phi0=2e-5)
+    nz, ny, nx = shape
+    basis = torch.from_numpy(inputs.radial_basis(shape, ((ny - 1) / 2.0, (nx - 1) / 2.0), R0, 16))
+    a, a_t = inputs.flux_fit_parameters(16)
+    return case, basis.to(device=dev, dtype=dtype), a, a_t
+
+
+def fit_loss(V, dVt):
+    return ((V[0] - V[1:] - dVt) ** 2).sum()
+
+
+def run_adjoint(args, dev):
+    """One iteration of the flux fit (forward run with checkpoints, loss, reverse sweep) in FP32
+    on the full sessile cap; throughput as MLUPS-equivalent = cells x steps / (forward + backward)."""
+    import torch
+    from paper_2412_14859_gb300.adjoint import volume_history
+    from paper_2412_14859_gb300.binding import Sim
+    T, K = args.adjoint_steps, 64
+    shape = tuple(int(v) for v in args.adjoint_shape.split(","))
+    case, basis, a, a_t = cap_fit(shape, 48.0 * shape[2] / 256.0, dev, torch.float64)
+    rn = torch.from_numpy(case.phase()).to(dev)
+
+    def phi_of(av):
+        return case.phi * (1.0 + torch.tensordot(av, basis, dims=1))
+
+    tgt = Sim.from_case(case, "f32")
+    tgt.init_equilibrium(rn)
+    tgt.set_flux(0.0, phi_of(torch.tensor(a_t, device=dev)).contiguous())
+    Vt = tgt.adjoint_forward(T, K)
+    dVt = (Vt[0] - Vt[1:]).detach()
+    tgt.close()
+    sim = Sim.from_case(case, "f32")
+    sim.init_equilibrium(rn)
+    at = torch.tensor(a, device=dev, requires_grad=True)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(s)
+    V = volume_history(sim, phi_of(at), T, K)
+    ev[1].record(s)
+    L = fit_loss(V, dVt)
+    L.backward()
+    ev[2].record(s)
+    torch.cuda.synchronize()
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    cells = sim.fluid_cells
+    sb = sim.bytes_per_update  # per update of the forward step
+    out = {
+        "workload": "D3Q19 sessile cap R0=%g, %dx%dx%d, walls on z, FP32, %d steps, "
+                    "checkpoint every %d, 16 flux coefficients" % (case.R0, shape[2], shape[1],
+                                                                   shape[0], T, K),
+        "mlups_equivalent": round(cells * T / ((fwd + bwd) / 1e3) / 1e6, 1),
+        "forward_ms": round(fwd, 1), "backward_ms": round(bwd, 1),
+        "backward_over_forward": round(bwd / fwd, 2),
+        "loss": float(L.detach()), "grad_norm": float(at.grad.norm()),
+        "tape_states": -(-T // K) + K + 3, "forward_bytes_per_update": sb,
+        "launches": "forward: 1 step + 1 volume kernel per step; backward per step: 1 recomputed "
+                    "step + 3 adjoint kernels",
+    }
+    sim.close()
+    return out
+
+
+def run_adjoint_fd(args):
+    """Gradient of the flux-fit loss vs central differences (h = 1e-3), FP64: the full cap over
+    256 steps and a reduced cap (64x64x32, R0 = 12) over 200 steps; site sets replayed from the
+    base run (the gate) and, for the reduced cap, also left free (reported)."""
+    import numpy as np
+    import torch
+    from paper_2412_14859_gb300.adjoint import volume_history
+    from paper_2412_14859_gb300.binding import SITES_GIVEN, Sim
+    dev = torch.device("cuda", 0)
+    report = {}
+    for name, shape, R0, T, K in (("reduced_64x64x32_R12", (32, 64, 64), 12.0, 200, 64),
+                                  ("full_256x256x128_R48", (128, 256, 256), 48.0, 256, 16)):
+        case, basis, a, a_t = cap_fit(shape, R0, dev, torch.float64)
+        rn = torch.from_numpy(case.phase()).to(dev)
+
+        def phi_of(av):
+            return (case.phi * (1.0 + torch.tensordot(torch.as_tensor(av, device=dev), basis, dims=1))).contiguous()
+
+        def run(av, rule=None, masks=None, record=False):
+            sim = Sim.from_case(case, "f64") if rule is None else Sim(
+                case.q, shape[2], shape[1], shape[0], case.periodic, case.rho_r_in, case.rho_b_in,
+                case.tau_r, case.tau_b, case.sigma, case.beta, rule, case.threshold, case.sbar, "f64")
+            sim.init_equilibrium(rn)
+            sim.set_flux(0.0, phi_of(av))
+            V, rec = [sim.volume()], []
+            for t in range(T):
+                if masks is not None:
+                    sim.set_mask(masks[t])
+                sim.step(1)
+                V.append(sim.volume())
+                if record:
+                    rec.append(sim.mask())
+            sim.close()
+            return torch.cat(V), rec
+
+        Vt, _ = run(a_t)
+        dVt = Vt[0] - Vt[1:]
+        sim = Sim.from_case(case, "f64")
+        sim.init_equilibrium(rn)
+        at = torch.tensor(a, device=dev, requires_grad=True)
+        t0 = time.perf_counter()
+        L = fit_loss(volume_history(sim, case.phi * (1.0 + torch.tensordot(at, basis, dims=1)), T, K), dVt)
+        L.backward()
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        sim.close()
+        grad = at.grad.cpu().numpy()
+        _, masks = run(a, record=True)
+        h = 1e-3
+        fd, fd_free = np.zeros(16), np.zeros(16)
+        for k in range(16):
+            e = np.zeros(16)
+            e[k] = h
+            fd[k] = (float(fit_loss(run(a + e, SITES_GIVEN, masks)[0], dVt)) -
+                     float(fit_loss(run(a - e, SITES_GIVEN, masks)[0], dVt))) / (2 * h)
+            if name.startswith("reduced"):
+                fd_free[k] = (float(fit_loss(run(a + e)[0], dVt)) - float(fit_loss(run(a - e)[0], dVt))) / (2 * h)
+        del masks
+        torch.cuda.empty_cache()
+        r = {"steps": T, "ckpt_every": K, "loss": float(L.detach()), "adjoint_s": round(t_adj, 2),
+             "grad": [float(v) for v in grad], "fd_replayed_sites": [float(v) for v in fd],
+             "max_abs_err_over_max_fd": float(np.max(np.abs(grad - fd)) / np.max(np.abs(fd))),
+             "max_rel_err_per_component": float(np.max(np.abs(grad - fd) / np.abs(fd)))}
+        if name.startswith("reduced"):
+            r["fd_free_sites"] = [float(v) for v in fd_free]
+            r["free_sites_err_over_max_fd"] = float(np.max(np.abs(grad - fd_free)) / np.max(np.abs(fd_free)))
+        report[name] = r
+    print(json.dumps({"adjoint_fd": report}), flush=True)
+
+
 def run_ours(args, d: Dist):
     import numpy as np
     import torch
@@ -388,6 +537,7 @@ def run_ours(args, d: Dist):
         sim.close()
 
     ensemble = run_ensemble(args, dev) if args.ensemble_steps > 0 else None
+    adjoint = run_adjoint(args, dev) if args.adjoint_steps > 0 else None
     if d.rank != 0:
         return
     traffic = ncu_traffic(head, args.size)
@@ -414,6 +564,8 @@ def run_ours(args, d: Dist):
     }
     if ensemble:
         line["ensemble"] = ensemble
+    if adjoint:
+        line["adjoint"] = adjoint
     if H["clocks"]:
         line["clocks"] = H["clocks"]
     if e2e:
@@ -427,6 +579,9 @@ def main():
     args = parse()
     if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) != args.gpus:
         sys.exit("--gpus N > 1 must be launched with torchrun --nproc-per-node N")
+    if args.adjoint_fd:
+        run_adjoint_fd(args)
+        return
     if args.impl == "reference":
         d = Dist("gloo")
         try:

@@ -16,6 +16,11 @@ method summary:
 
 The observable is the liquid volume V = sum over fluid cells of (1 + rho^N)/2 of a stored state.
 
+Where w_r w_b < BULK_TRACE (bulk: one colour is a trace) the recoloring direction F/|F| is held
+fixed for differentiation (its value is unchanged): in the bulk that direction is undefined at
+F = 0 and the linearised dynamics of trace densities through it is scale-invariant and unstable,
+so the exact tangent there says nothing about finite perturbations of the flux.
+
 Pins (tests/test_oracle_adjoint.py): its states equal the C oracle's step for step; its gradient
 equals central finite differences of the C oracle replaying the same site sets; and for one
 step it equals the closed form dV(1)/dphi(x) = -m(x) / (rho(x) S-bar).
@@ -30,6 +35,7 @@ import torch
 from . import RULE_GIVEN, Params, Run, alphas, lattice
 
 torch_dtype = torch.float64
+BULK_TRACE = 1e-6
 
 
 class Geometry:
@@ -117,6 +123,7 @@ def step(geo: Geometry, f: torch.Tensor, phi: torch.Tensor, site: torch.Tensor) 
     iFn = torch.where(pos, 1.0 / Fn_safe, torch.zeros_like(F2))
     uu = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
     amp = 9.0 * p.sigma / 4.0
+    bulk = (rr / rho) * (rb / rho) < BULK_TRACE
     out_r, out_b = [], []
     for i in range(Q):
         cu = sum(c[i][d] * u[d] for d in range(3))
@@ -127,6 +134,7 @@ def step(geo: Geometry, f: torch.Tensor, phi: torch.Tensor, site: torch.Tensor) 
         fi = fi + amp * itau * (geo.W[i] * Fc * Fc * iFn - geo.C[i] * Fn)   # Eq. (perturb)
         norm = float(np.sqrt(sum(v * v for v in c[i])))
         cos = Fc * iFn / norm if i else torch.zeros_like(rho)
+        cos = torch.where(bulk, cos.detach(), cos)
         fr = (rr / rho) * fi + p.beta * (rr * rb / (rho * rho)) * cos * rest  # Eq. (recolor)
         out_r.append(torch.where(geo.fluid, fr, torch.zeros_like(fr)))
         out_b.append(torch.where(geo.fluid, fi - fr, torch.zeros_like(fr)))

@@ -26,6 +26,9 @@
 
 namespace cgevap {
 
+// Minority fraction product w_r w_b below which the adjoint holds the recoloring direction fixed.
+constexpr double kBulkTrace = 1e-6;
+
 // Pull source of direction i from the cell with slot sl at storage index si (see pull_cell).
 template <class L>
 __device__ __forceinline__ int pull_source(const Slot& sl, const PlaneOffsets& po, int si, int i) {
@@ -78,7 +81,7 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   const R amp = (R)ph.amp, beta = (R)ph.beta;
   const R pamp = amp * itau;
   const R rcol = beta * wr * wb;
-  R restc[3], rwc[3], kw[3], kc[3], kr[3], nrm[3], As[3], Bs[3], Ws[3], Cs[3];
+  R restc[3], rwc[3], nrm[3], As[3], Bs[3], Ws[3], Cs[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int i = c == 0 ? 0 : (c == 1 ? 1 : L::Q - 1);
@@ -89,16 +92,24 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
     nrm[c] = R(inv_norm<L>(i));
     restc[c] = rho * (As[c] + Bs[c] * abar);
     rwc[c] = rho * Ws[c];
-    kw[c] = pamp * Ws[c] * iFn;
-    kc[c] = pamp * Cs[c] * Fn;
-    kr[c] = rcol * iFn * nrm[c] * restc[c];
   }
 
-  // Backwards through recolor -> perturb -> collision -> feq, direction by direction.
-  R A_wr = R(0), A_itau = R(0), A_uu15 = R(0);
-  R A_kr[3] = {R(0), R(0), R(0)}, A_kw[3] = {R(0), R(0), R(0)}, A_kc[3] = {R(0), R(0), R(0)};
+  // Backwards through recolor -> perturb -> collision -> feq, direction by direction.  The
+  // F-dependence is carried by |F| and the unit vector e = F/|F| (nc_i = e.c_i), both bounded:
+  //   perturbation  pamp (W_s |F| nc_i^2 - C_s |F|)   -> d/dF = pamp (2 W_s nc_i c_i - (W_s nc_i^2 + C_s) e)
+  //   recoloring    rcol nrm_s restc_s nc_i          -> d/dF = rcol nrm_s restc_s (c_i - nc_i e) / |F|
+  // so 1/|F| enters once (as in the step itself); far from an interface |F| can be tiny.
+  // Where w_r w_b < kBulkTrace (bulk: one colour is a trace) the recoloring direction e is held
+  // fixed: that term is homogeneous of degree 1 in the trace, so its derivative with respect to F
+  // stays O(beta w_r / |F|) however small the trace, and the linearised trace dynamics grows
+  // without bound while the traces themselves stay negligible.
+  R A_wr = R(0), A_itau = R(0), A_uu15 = R(0), A_pamp = R(0), A_rcol = R(0);
   R A_rwc[3] = {R(0), R(0), R(0)}, A_restc[3] = {R(0), R(0), R(0)};
-  R Aua = R(0), Aub = R(0), Aum = R(0), AFa = R(0), AFb = R(0), AFm = R(0);
+  R Aua = R(0), Aub = R(0), Aum = R(0);
+  R Pa = R(0), Pb = R(0), Pm = R(0);  // sum_i 2 pamp W_s q_i nc_i c_i
+  R Ga = R(0), Gb = R(0), Gm = R(0);  // sum_i g_i c_i, g_i = d_i rcol nrm_s restc_s
+  R Sn = R(0), Sg = R(0);             // sum_i q_i (W_s nc_i^2 + C_s), sum_i g_i nc_i
+  const bool bulk = wr * wb < R(kBulkTrace);
   R Af[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -110,18 +121,23 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
     if (L::cb(i) < 0) { cu -= ub; pc -= Fb; }
     if (L::cm(i) > 0) { cu += um; pc += Fm; }
     if (L::cm(i) < 0) { cu -= um; pc -= Fm; }
+    const R nc = pc * iFn;  // e.c_i (0 where F = 0)
     const R poly = cu * (R(4.5) * cu + R(3)) - uu15;
     const R feq = rwc[c] * poly + restc[c];
-    const R fi = f[i] + itau * (feq - f[i]) + kw[c] * pc * pc - kc[c];  // post-perturbation
-    // Eq. (recolor): f^{r*} = wr fi + kr pc, f^{b*} = fi - f^{r*}
+    const R pert = Ws[c] * Fn * nc * nc - Cs[c] * Fn;  // perturbation shape, Eq. (perturb)
+    const R fi = f[i] + itau * (feq - f[i]) + pamp * pert;  // post-perturbation
+    // Eq. (recolor): f^{r*} = wr fi + rcol nrm restc nc, f^{b*} = fi - f^{r*}
     const R d = lam[i].r - lam[i].b;
     const R q = wr * d + lam[i].b;  // dL/dfi
     A_wr += d * fi;
-    A_kr[c] += d * pc;
-    // Eq. (perturb): fi += kw pc^2 - kc
-    const R A_pc = d * kr[c] + R(2) * q * kw[c] * pc;
-    A_kw[c] += q * pc * pc;
-    A_kc[c] -= q;
+    A_rcol += d * nrm[c] * restc[c] * nc;
+    A_restc[c] += d * rcol * nrm[c] * nc;
+    const R g = bulk ? R(0) : d * rcol * nrm[c] * restc[c];
+    Sg += g * nc;
+    // Eq. (perturb)
+    A_pamp += q * pert;
+    Sn += q * (Ws[c] * nc * nc + Cs[c]);
+    const R p2 = R(2) * pamp * Ws[c] * q * nc;
     // Eq. (collision): fi = f + itau (feq - f)
     const R A_feq = q * itau;
     Af[i] = q * (R(1) - itau);
@@ -131,29 +147,23 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
     A_restc[c] += A_feq;
     const R A_cu = A_feq * rwc[c] * (R(9) * cu + R(3));
     A_uu15 -= A_feq * rwc[c];
-    if (L::ca(i) > 0) { Aua += A_cu; AFa += A_pc; }
-    if (L::ca(i) < 0) { Aua -= A_cu; AFa -= A_pc; }
-    if (L::cb(i) > 0) { Aub += A_cu; AFb += A_pc; }
-    if (L::cb(i) < 0) { Aub -= A_cu; AFb -= A_pc; }
-    if (L::cm(i) > 0) { Aum += A_cu; AFm += A_pc; }
-    if (L::cm(i) < 0) { Aum -= A_cu; AFm -= A_pc; }
+    if (L::ca(i) > 0) { Aua += A_cu; Pa += p2; Ga += g; }
+    if (L::ca(i) < 0) { Aua -= A_cu; Pa -= p2; Ga -= g; }
+    if (L::cb(i) > 0) { Aub += A_cu; Pb += p2; Gb += g; }
+    if (L::cb(i) < 0) { Aub -= A_cu; Pb -= p2; Gb -= g; }
+    if (L::cm(i) > 0) { Aum += A_cu; Pm += p2; Gm += g; }
+    if (L::cm(i) < 0) { Aum -= A_cu; Pm -= p2; Gm -= g; }
   }
-  // Speed-class factors: kr = rcol iFn nrm restc, kw = pamp W iFn, kc = pamp C |F|,
-  // restc = rho (A + B abar), rwc = rho W.
-  R A_rcol = R(0), A_iFn = R(0), A_Fn = R(0), A_pamp = R(0), A_rho = R(0), A_abar = R(0);
+  // restc_s = rho (A_s + B_s abar), rwc_s = rho W_s
+  R A_rho = R(0), A_abar = R(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    A_rcol += A_kr[c] * iFn * nrm[c] * restc[c];
-    A_iFn += A_kr[c] * rcol * nrm[c] * restc[c] + A_kw[c] * pamp * Ws[c];
-    const R A_rc = A_restc[c] + A_kr[c] * rcol * iFn * nrm[c];
-    A_pamp += A_kw[c] * Ws[c] * iFn + A_kc[c] * Cs[c] * Fn;
-    A_Fn += A_kc[c] * pamp * Cs[c];
-    A_rho += A_rc * (As[c] + Bs[c] * abar) + A_rwc[c] * Ws[c];
-    A_abar += A_rc * rho * Bs[c];
+    A_rho += A_restc[c] * (As[c] + Bs[c] * abar) + A_rwc[c] * Ws[c];
+    A_abar += A_restc[c] * rho * Bs[c];
   }
-  A_itau += A_pamp * amp;
+  A_itau += A_pamp * amp;  // pamp = amp itau
   R A_wb = R(0);
-  A_wr += A_rcol * beta * wb + A_itau * ir + A_abar * (R)ph.alpha_r;
+  A_wr += A_rcol * beta * wb + A_itau * ir + A_abar * (R)ph.alpha_r;  // rcol = beta wr wb
   A_wb += A_rcol * beta * wr + A_itau * ib + A_abar * (R)ph.alpha_b;
   // u = j / rho, uu15 = 3/2 |u|^2
   Aua += R(3) * A_uu15 * ua;
@@ -161,16 +171,12 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   Aum += R(3) * A_uu15 * um;
   A_rho -= (Aua * ua + Aub * ub + Aum * um) * irho;
   const R Aja = Aua * irho, Ajb = Aub * irho, Ajm = Aum * irho;
-  // |F| and 1/|F| as functions of F (zero where F = 0, as in the step)
-  if (F2 > R(0)) {
-    const R s = (A_Fn - A_iFn * iFn * iFn) * iFn;
-    AFa += s * Fa;
-    AFb += s * Fb;
-    AFm += s * Fm;
-  }
-  lF[0] = AFa;
-  lF[1] = AFb;
-  lF[2] = AFm;
+  // dL/dF = P - pamp Sn e + (G - Sg e) / |F|, e = F / |F| (zero where F = 0, as in the step)
+  const R ea = Fa * iFn, eb = Fb * iFn, em = Fm * iFn;
+  const R se = pamp * Sn + Sg * iFn;
+  lF[0] = Pa + Ga * iFn - se * ea;
+  lF[1] = Pb + Gb * iFn - se * eb;
+  lF[2] = Pm + Gm * iFn - se * em;
   // wr = rr / rho, wb = rb / rho, rho = rr + rb
   const R A_rr = A_rho + (A_wr - A_wb) * wb * irho;
   const R A_rb = A_rho + (A_wb - A_wr) * wr * irho;

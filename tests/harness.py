@@ -45,10 +45,15 @@ def gpu_sim(case: inputs.Case, storage: str, phi_field=None, solid=None, kernel=
     return sim
 
 
-def adjoint_case(q):
+def adjoint_case(q, bulk=False):
     """Small lattice with sites, walls and (3D) one solid cell, a seeded flux field and a noisy
-    initial state: (oracle params, f0, phi field)."""
-    if q == 9:  # D2Q9 drop touching nothing, walls across y
+    initial state: (oracle params, f0, phi field).  bulk: a D2Q9 box large enough that its far
+    field holds cells where one colour is a trace (w_r w_b < 1e-6)."""
+    if q == 9 and bulk:
+        shape = (1, 40, 64)
+        per = (1, 0, 1)
+        phase = inputs.sphere_phase(shape, (0.0, 19.5, 31.5), 8.0)
+    elif q == 9:  # D2Q9 drop touching nothing, walls across y
         shape = (1, 14, 17)
         per = (1, 0, 1)
         phase = inputs.sphere_phase(shape, (0.0, 6.5, 8.0), 4.5)

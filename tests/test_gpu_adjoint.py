@@ -30,11 +30,14 @@ def sim_for(p, storage, rule=None):
     return sim
 
 
-@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("q,bulk", [(9, False), (19, False), (9, True)])
 @pytest.mark.parametrize("storage,tol,vtol", [("f64", 1e-10, 1e-13), ("f32", 2e-3, 1e-6)])
-def test_adjoint_matches_autograd_oracle(q, storage, tol, vtol):
-    p, f0, phi = adjoint_case(q)
-    T = STEPS[q]
+def test_adjoint_matches_autograd_oracle(q, bulk, storage, tol, vtol):
+    p, f0, phi = adjoint_case(q, bulk)
+    T = 24 if bulk else STEPS[q]
+    if bulk:  # the far field holds trace cells, where the recoloring direction is held fixed
+        rr, rb = f0[0].sum(0), f0[1].sum(0)
+        assert np.count_nonzero(rr * rb / (rr + rb) ** 2 < AR.BULK_TRACE) > 100
     sites = AR.record_sites(p, f0, T)
     w = inputs.rng(inputs.SEED + 21).normal(size=T + 1)
     ph = torch.tensor(phi, requires_grad=True)
