@@ -183,6 +183,22 @@ CGEVAP_API int cgevap_check_health(cgevap_sim* sim);
 CGEVAP_API int cgevap_save(cgevap_sim* sim, const char* path);
 CGEVAP_API int cgevap_load(cgevap_sim* sim, const char* path);
 
+/* Site threshold for a target S-bar (Sec. II.B): the threshold (Gamma for the gradient rule,
+ * theta for the band rule) at which an evaporating flat interface loses mass at the prescribed
+ * rate, Eq. (satisfy) with Eq. (relation): the time-averaged number of sites per step equals
+ * target_sbar x A.  Procedure: a flat interface normal to y on p's box (red below y = 5 ny/8,
+ * tanh profile; A = nx nz, or 2 nx nz with a periodic y axis) is equilibrated with the flux off
+ * until u changes by less than 1e-7 over 100 steps (at most 5000 steps, Sec. III), then for each
+ * trial threshold an evaporation run with flux phi from that state to t* = 1/2 (the interface
+ * recedes by half its height) gives the mean site count; the threshold is bisected (30 trials)
+ * until that count matches.  p supplies the physics, box, site rule and storage (F64 or F32;
+ * p->threshold and p->sbar are not used).  out_threshold: the threshold; out_sbar (may be NULL):
+ * the S-bar measured at it.  Synchronous; allocates and frees its own handle.  Errors (message in
+ * cgevap_last_error(NULL)): ARG (NULL pointers, phi or target_sbar not > 0, ny < 16, a target
+ * outside what any threshold reaches), UNSUPPORTED (16-bit storage), OOM, CUDA. */
+CGEVAP_API int cgevap_calibrate_threshold(const cgevap_params* p, double phi, double target_sbar,
+                                          double* out_threshold, double* out_sbar);
+
 /* Select the fused-step kernel: family -1 automatic (the default at create: currently the
  * register-pipelined kernel, measured faster), 0 the
  * register-pipelined kernel (every storage, any nx), 1 the bulk-copy pipelined kernel (FP32

@@ -66,6 +66,9 @@ _SIGS = {
     "cgevap_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cgevap_get_macros": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "cgevap_get_mask": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_calibrate_threshold": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_double,
+                                                  ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double)]),
     "cgevap_set_mask": (ctypes.c_int, [_vp, _vp]),
     "cgevap_volume": (ctypes.c_int, [_vp, _vp]),
     "cgevap_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
@@ -324,6 +327,23 @@ class Sim:
     @property
     def fluid_cells(self) -> int:
         return lib().cgevap_fluid_cells(self._h)
+
+
+def calibrate_threshold(q: int, nx: int, ny: int, nz: int = 1, periodic=(1, 0, 1), phi: float = 0.03,
+                        target_sbar: float = 3.0, rho_r_in: float = 1.0, rho_b_in: float = 1.0,
+                        tau_r: float = 1.0, tau_b: float = 1.0, sigma: float = 0.0, beta: float = 0.7,
+                        site_rule: int = SITES_GRADIENT, storage="f64"):
+    """Threshold for a target S-bar on an evaporating flat interface (cgevap_calibrate_threshold);
+    returns (threshold, measured S-bar)."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p = Params(q, nx, ny, nz, (ctypes.c_int * 3)(*periodic), rho_r_in, rho_b_in, tau_r, tau_b, sigma,
+               beta, site_rule, 0.0, target_sbar, st)
+    thr, sb = ctypes.c_double(), ctypes.c_double()
+    rc = lib().cgevap_calibrate_threshold(ctypes.byref(p), float(phi), float(target_sbar),
+                                          ctypes.byref(thr), ctypes.byref(sb))
+    if rc != 0:
+        raise CgevapError(rc, lib().cgevap_last_error(None).decode())
+    return thr.value, sb.value
 
 
 def all_signatures():

@@ -227,16 +227,21 @@ int launch_one_step(cgevap_sim* s) {
   return CGEVAP_OK;
 }
 
-int refresh_gradient_sites(cgevap_sim* s) {
+
+}  // namespace
+
+int cgevap::refresh_gradient_sites(cgevap_sim* s) {
   if (s->p.site_rule != CGEVAP_SITES_GRADIENT) {
     CG_CUDA(s, cudaMemsetAsync(s->mask[s->cur], 0, s->N, s->stream));
     return CGEVAP_OK;
   }
   if (!s->tmp_rn && cudaMalloc(&s->tmp_rn, s->N * sizeof(double)) != cudaSuccess)
-    return fail(s, CGEVAP_ERR_OOM, "cannot allocate rho^N scratch");
+    return sim_fail(s, CGEVAP_ERR_OOM, "cannot allocate rho^N scratch");
   CG_CUDA(s, launch_gradient_sites(aux_of(s), s->state[s->cur], s->tmp_rn, s->mask[s->cur], s->stream));
   return CGEVAP_OK;
 }
+
+namespace {
 
 void release(cgevap_sim* s) {
   if (!s) return;

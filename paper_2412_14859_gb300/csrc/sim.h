@@ -56,6 +56,9 @@ int sim_fail(cgevap_sim* s, int code, const std::string& msg);
 AuxArgs aux_of(const cgevap_sim* s);
 // Arguments of one fused step of the current plan, reading state[cur] and writing state[cur^1].
 StepArgs step_args(cgevap_sim* s);
+// Site bytes read by the next step, recomputed from the current state: under the gradient rule
+// bit 1 = |F| of the state > threshold (the "previous step" decision before a first step), else 0.
+int refresh_gradient_sites(cgevap_sim* s);
 // Adjoint tape release (adjoint.cu), called when the handle is destroyed.
 void adjoint_release(cgevap_sim* s);
 }  // namespace cgevap

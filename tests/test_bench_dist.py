@@ -1,0 +1,85 @@
+"""Host logic of bench.py on CPU: the multi-rank aggregation (gloo, world size 2, spawned
+processes) and the reference arm's rank handling and JSON line."""
+import importlib.util
+import io
+import json
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+from types import SimpleNamespace
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    b = load_bench()
+    d = b.Dist("gloo")
+    try:
+        # rank r updates 1000 + r cells for 10 steps in 5 + r ms
+        mlups, ms = b.aggregate(1000 + rank, 10, 5.0 + rank, d)
+        d.barrier()
+        q.put((rank, mlups, ms))
+    finally:
+        d.close()
+
+
+def test_aggregate_is_whole_job_over_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    want_ms = 6.0
+    want = (1000 + 1001) * 10 / (want_ms / 1e3) / 1e6
+    for rank, mlups, ms in got:
+        assert ms == pytest.approx(want_ms)
+        assert mlups == pytest.approx(want)
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    b = load_bench()
+    d = SimpleNamespace(rank=1, world=2)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert b.run_reference(SimpleNamespace(steps=1, warmup=0, size=12), d) is None
+    assert buf.getvalue() == ""
+
+
+def test_reference_arm_line(oracle_lib):
+    b = load_bench()
+    d = SimpleNamespace(rank=0, world=1)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        b.run_reference(SimpleNamespace(steps=2, warmup=1, size=12), d)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["steps"] == 2 and line["warmup"] == 1
