@@ -38,10 +38,11 @@ __device__ __forceinline__ int pull_source(const Slot& sl, const PlaneOffsets& p
 }
 
 // (1) for one cell: recompute the moments, F and the per-direction terms of collide_store and
-// run them backwards.  g: post-exchange populations; lam: dL/d(f^{r*}, f^{b*}) of this cell;
+// run them backwards.  fcb: colour-blind sums of the post-exchange populations (rho_r, rho_b
+// given separately); lam: dL/d(f^{r*}, f^{b*}) of this cell;
 // out: lg = dL/dg through this cell's own collision, lF = dL/dF.
 template <int Q, class R>
-__device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (&g)[Q], R rr, R rb,
+__device__ __forceinline__ void collide_adjoint(const Physics& ph, const R (&fcb)[Q], R rr, R rb,
                                                 R irho, const R (&rnb)[Q], const V2<R> (&lam)[Q],
                                                 V2<R> (&lg)[Q], R (&lF)[3]) {
   using L = Lattice<Q>;
@@ -51,7 +52,7 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   R ja = R(0), jb = R(0), jm = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    f[i] = g[i].r + g[i].b;
+    f[i] = fcb[i];
     if (L::ca(i) > 0) ja += f[i];
     if (L::ca(i) < 0) ja -= f[i];
     if (L::cb(i) > 0) jb += f[i];
@@ -61,9 +62,9 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   }
   const R ua = ja * irho, ub = jb * irho, um = jm * irho;
   const R uu15 = R(1.5) * (ua * ua + ub * ub + um * um);
-  const R ir = (R)ph.inv_tau_r, ib = (R)ph.inv_tau_b;
+  const R ir = PHYS(R, ph, inv_tau_r), ib = PHYS(R, ph, inv_tau_b);
   const R itau = wr * ir + wb * ib;
-  const R abar = wr * (R)ph.alpha_r + wb * (R)ph.alpha_b;
+  const R abar = wr * PHYS(R, ph, alpha_r) + wb * PHYS(R, ph, alpha_b);
   R Fa = R(0), Fb = R(0), Fm = R(0);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
@@ -78,7 +79,7 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   const R F2 = Fa * Fa + Fb * Fb + Fm * Fm;
   R Fn = R(0), iFn = R(0);
   if (F2 > R(0)) norm_pair<R>(F2, Fn, iFn);
-  const R amp = (R)ph.amp, beta = (R)ph.beta;
+  const R amp = PHYS(R, ph, amp), beta = PHYS(R, ph, beta);
   const R pamp = amp * itau;
   const R rcol = beta * wr * wb;
   R restc[3], rwc[3], nrm[3], As[3], Bs[3], Ws[3], Cs[3];
@@ -163,8 +164,8 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const V2<R> (
   }
   A_itau += A_pamp * amp;  // pamp = amp itau
   R A_wb = R(0);
-  A_wr += A_rcol * beta * wb + A_itau * ir + A_abar * (R)ph.alpha_r;  // rcol = beta wr wb
-  A_wb += A_rcol * beta * wr + A_itau * ib + A_abar * (R)ph.alpha_b;
+  A_wr += A_rcol * beta * wb + A_itau * ir + A_abar * PHYS(R, ph, alpha_r);  // rcol = beta wr wb
+  A_wb += A_rcol * beta * wr + A_itau * ib + A_abar * PHYS(R, ph, alpha_b);
   // u = j / rho, uu15 = 3/2 |u|^2
   Aua += R(3) * A_uu15 * ua;
   Aub += R(3) * A_uu15 * ub;
@@ -199,7 +200,7 @@ struct AdjointEpilogue {
   AdjointOut o;
   template <int Q, int S, class R>
   __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, int si, int /*nimg*/,
-                                       const int (&)[3], const V2<R> (&g)[Q], R rr, R rb, R irho,
+                                       const int (&)[3], const R (&g)[Q], R rr, R rb, R irho,
                                        R /*e*/, uint32_t /*flags*/, const R (&rnb)[Q],
                                        long long&, double&) const {
     using Vec = typename Storage<S>::vec;

@@ -103,6 +103,7 @@ AuxArgs cgevap::aux_of(const cgevap_sim* s) {
   AuxArgs a;
   a.g = s->geom;
   a.ph = s->ph;
+  mirror_floats(a.ph);
   a.q = s->p.q;
   a.storage = s->p.storage;
   a.rho_r_in = s->p.rho_r_in;
@@ -201,6 +202,7 @@ StepArgs cgevap::step_args(cgevap_sim* s) {
   std::memset(&a, 0, sizeof(a));
   a.g = s->geom;
   a.ph = s->ph;
+  mirror_floats(a.ph);
   a.red.part_removed = s->part_removed;
   a.red.part_sites = s->part_sites;
   a.red.done = s->done;
@@ -274,6 +276,7 @@ int sim_view(cgevap_sim* s, SimView* v) {
   if (!s || !v) return CGEVAP_ERR_ARG;
   v->g = s->geom;
   v->ph = s->ph;
+  mirror_floats(v->ph);
   v->state[0] = s->state[0];
   v->state[1] = s->state[1];
   v->mask[0] = s->mask[0];

@@ -73,7 +73,28 @@ struct Physics {
   const void* phi_field;         // per-cell phi (double for ST_F64, float otherwise) or nullptr
   float kap_r[19], kap_b[19];    // deviation storage: phi_i(alpha_k) / phi_0(alpha_k)
   float scale, inv_scale;        // deviation storage: power-of-two scale of the deviations
+  // FP32 copies of the constants above (rounded to nearest, as a device-side conversion would
+  // round them), so FP32 kernels execute no FP64 instruction; filled by mirror_floats().
+  float f_inv_tau_r, f_inv_tau_b, f_alpha_r, f_alpha_b, f_amp, f_beta, f_threshold, f_varphi,
+      f_inv_sbar;
 };
+
+// Refresh the FP32 copies; every launch that passes a Physics to a kernel calls this first.
+__host__ __device__ inline void mirror_floats(Physics& ph) {
+  ph.f_inv_tau_r = (float)ph.inv_tau_r;
+  ph.f_inv_tau_b = (float)ph.inv_tau_b;
+  ph.f_alpha_r = (float)ph.alpha_r;
+  ph.f_alpha_b = (float)ph.alpha_b;
+  ph.f_amp = (float)ph.amp;
+  ph.f_beta = (float)ph.beta;
+  ph.f_threshold = (float)ph.threshold;
+  ph.f_varphi = (float)ph.varphi;
+  ph.f_inv_sbar = (float)ph.inv_sbar;
+}
+
+// A physics constant in the kernel's real type R: the double for FP64 kernels, the FP32 copy
+// otherwise (the other branch is a compile-time dead one).
+#define PHYS(R, ph, name) (sizeof(R) == 8 ? (R)(ph).name : (R)(ph).f_##name)
 
 struct Reduce {
   double* part_removed;          // per-block partial sums (scratch, one slot per block)

@@ -83,6 +83,15 @@ struct Lattice<19> {
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// True when every odd direction i has its opposite at i + 1 (checked where code relies on it).
+template <class L>
+__host__ __device__ constexpr bool opposites_adjacent() {
+  for (int i = 1; i + 1 < L::Q; i += 2)
+    if (L::ca(i + 1) != -L::ca(i) || L::cb(i + 1) != -L::cb(i) || L::cm(i + 1) != -L::cm(i))
+      return false;
+  return (L::Q & 1) == 1;
+}
+
 // 1/|c_i| for the recoloring angle (0 for the rest direction, whose cos is defined as 0).
 template <class L>
 __host__ __device__ constexpr double inv_norm(int i) {

@@ -141,6 +141,7 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
   ph.inv_sbar = 1.0 / p->sbar;
   ph.varphi = phi / p->sbar;
   ph.phi_field = nullptr;
+  mirror_floats(ph);
   if (p->q == 19)
     kappa_of<19>(ph);
   else

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_dev_kernel(const __grid_
                           cur[c].rb, cur[c].irho, rnb, Fn);
       uint32_t mb = cur[c].flags;
       if (A.ph.rule == 0) {
-        const R d = Fn - (R)A.ph.threshold;
+        const R d = Fn - PHYS(R, A.ph, threshold);
         mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
       }
       A.mask_out[cell] = (uint8_t)mb;

@@ -112,8 +112,8 @@ __device__ __forceinline__ bool solid_bits(const Geom& g, const Slot& s, const P
 template <int S>
 __device__ __forceinline__ typename Storage<S>::real flux_at(const Physics& ph, int cell) {
   using R = typename Storage<S>::real;
-  if (ph.phi_field == nullptr) return (R)ph.varphi;
-  return (R)__ldg(reinterpret_cast<const R*>(ph.phi_field) + cell) * (R)ph.inv_sbar;
+  if (ph.phi_field == nullptr) return PHYS(R, ph, varphi);
+  return (R)__ldg(reinterpret_cast<const R*>(ph.phi_field) + cell) * PHYS(R, ph, inv_sbar);
 }
 
 template <class R>
@@ -146,7 +146,7 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
   const R rn_pre = (sr - sb) * irho;
   bool site, near;
   if (A.ph.rule == 1) {
-    const R d = fabs(rn_pre) - (R)A.ph.threshold;
+    const R d = fabs(rn_pre) - PHYS(R, A.ph, threshold);
     site = d < R(0);
     near = fabs(d) < R(1e-6);
   } else {
@@ -188,17 +188,24 @@ __device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int
                                           V2<typename Storage<S>::real> (&g)[Q]) {
   using L = Lattice<Q>;
   using IO = PopIO<S, Q>;
+  if (sbits == 0) {  // no link of this cell bounces back (the common case)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                      (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                      (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+      g[i] = IO::load(A.pin, A.g.nstore, i, i, src, A.ph);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
               (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
               (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
-    int dir = i;
-    if (sbits) {
-      const bool bounce = (sbits >> i) & 1u;
-      src = bounce ? si : src;
-      dir = bounce ? opp(i) : i;
-    }
+    const bool bounce = (sbits >> i) & 1u;
+    src = bounce ? si : src;
+    const int dir = bounce ? opp(i) : i;
     g[i] = IO::load(A.pin, A.g.nstore, i, dir, src, A.ph);
   }
 }
@@ -261,15 +268,16 @@ __device__ __forceinline__ void norm_pair<float>(float F2, float& Fn, float& iFn
 }
 
 // Moments, Eq. (collision) with Eq. (feq), Eq. (perturb), Eq. (recolor); stores f^{k*} at the
-// cell's storage index si and its periodic ghost images si + dimg[j], j < nimg.
+// cell's storage index si and (GHOSTS: the kernel family that keeps periodic images) its ghost
+// images si + dimg[j], j < nimg.
 // rnb[i] is rho^N at x + c_i (the cell's own value where that neighbour is solid).  The factors
 // that depend only on the speed class s = |c_i|^2 are formed once per cell:
 //   f_i^eq = rho (A_s + B_s abar) + rho W_s (3 cu + 9/2 cu^2 - 3/2 u^2)            (Eq. feq)
 //   (9/4)(sigma/tau)|F|[W_s (F.c_i)^2/|F|^2 - C_s] = kw_s (F.c_i)^2 - kc_s        (Eq. perturb)
 //   beta (rho_r rho_b / rho^2) cos(theta_i) f_i^eq(rho, 0) = kr_s (F.c_i)          (Eq. recolor)
-template <int Q, int S>
+template <int Q, int S, bool GHOSTS = true>
 __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nimg, const int (&dimg)[3],
-                                              const V2<typename Storage<S>::real> (&g)[Q],
+                                              const typename Storage<S>::real (&fcb)[Q],
                                               typename Storage<S>::real rr,
                                               typename Storage<S>::real rb,
                                               typename Storage<S>::real irho,
@@ -285,7 +293,7 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   R ja = R(0), jb = R(0), jm = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    f[i] = g[i].r + g[i].b;  // colour-blind population
+    f[i] = fcb[i];  // colour-blind population
     if (L::ca(i) > 0) ja += f[i];
     if (L::ca(i) < 0) ja -= f[i];
     if (L::cb(i) > 0) jb += f[i];
@@ -295,8 +303,8 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   }
   const R ua = ja * irho, ub = jb * irho, um = jm * irho;
   const R uu15 = R(1.5) * (ua * ua + ub * ub + um * um);
-  const R itau = wr * (R)ph.inv_tau_r + wb * (R)ph.inv_tau_b;  // harmonic mean of tau_k
-  const R abar = wr * (R)ph.alpha_r + wb * (R)ph.alpha_b;
+  const R itau = wr * PHYS(R, ph, inv_tau_r) + wb * PHYS(R, ph, inv_tau_b);  // harmonic mean of tau_k
+  const R abar = wr * PHYS(R, ph, alpha_r) + wb * PHYS(R, ph, alpha_b);
   // Eq. (cg): F = (1/c_s^2) sum_i W_i rho^N(x + c_i) c_i
   R Fa = R(0), Fb = R(0), Fm = R(0);
 #pragma unroll
@@ -312,8 +320,8 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   const R F2 = Fa * Fa + Fb * Fb + Fm * Fm;
   R Fn = R(0), iFn = R(0);
   if (F2 > R(0)) norm_pair<R>(F2, Fn, iFn);
-  const R pamp = (R)ph.amp * itau;       // (9/4) sigma / tau
-  const R rcol = (R)ph.beta * wr * wb;   // beta rho_r rho_b / rho^2
+  const R pamp = PHYS(R, ph, amp) * itau;       // (9/4) sigma / tau
+  const R rcol = PHYS(R, ph, beta) * wr * wb;   // beta rho_r rho_b / rho^2
   R restc[3], rwc[3], kw[3], kc[3], kr[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -324,9 +332,21 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     kc[c] = pamp * R(L::C(i)) * Fn;
     kr[c] = rcol * iFn * R(inv_norm<L>(i)) * restc[c];
   }
-  V2<R> f0{R(0), R(0)};
+  // Rest direction: c_0 = 0, so Eq. (feq) is restc - rwc 3/2 u^2, the perturbation -kc and no
+  // recoloring term.
+  const R f0eq = fma(rwc[0], -uu15, restc[0]);
+  const R fi0 = fma(itau, f0eq - f[0], f[0]) - kc[0];
+  const V2<R> f0{wr * fi0, fi0 - wr * fi0};
+  IO::store(A.pout, A.g.nstore, 0, si, f0.r, f0.b, f0, ph);
+  if (GHOSTS && nimg)
+    for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0.r, f0.b, f0, ph);
+  static_assert(opposites_adjacent<L>(), "directions (i, i+1), i odd, must be opposite");
+  // Opposite directions (i, i+1) share |c.u|, |c.F| with opposite signs: the even part of Eq.
+  // (feq) and the perturbation are common, the odd part of Eq. (feq) and the recoloring term
+  // change sign.
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1;
     const int c = L::speed2(i);
     R cu = R(0), pc = R(0);
     if (L::ca(i) > 0) { cu += ua; pc += Fa; }
@@ -335,18 +355,40 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     if (L::cb(i) < 0) { cu -= ub; pc -= Fb; }
     if (L::cm(i) > 0) { cu += um; pc += Fm; }
     if (L::cm(i) < 0) { cu -= um; pc -= Fm; }
-    const R feq = fma(rwc[c], fma(cu, fma(R(4.5), cu, R(3)), -uu15), restc[c]);
-    R fi = fma(itau, feq - f[i], f[i]);                 // Eq. (collision)
-    fi = fma(kw[c], pc * pc, fi - kc[c]);               // Eq. (perturb)
-    const R fr = fma(wr, fi, kr[c] * pc);               // Eq. (recolor)
-    const R fb = fi - fr;
-    if (i == 0) f0 = {fr, fb};
-    IO::store(A.pout, A.g.nstore, i, si, fr, fb, f0, ph);
-    if (nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
-      for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, i, si + dimg[j], fr, fb, f0, ph);
+    const R even = fma(rwc[c], fma(R(4.5) * cu, cu, -uu15), restc[c]);
+    const R odd = R(3) * rwc[c] * cu;
+    const R pert = fma(kw[c], pc * pc, -kc[c]);  // Eq. (perturb), even in c
+    const R kp = kr[c] * pc;                     // Eq. (recolor) term, odd in c
+    const R fi = fma(itau, (even + odd) - f[i], f[i]) + pert;  // Eq. (collision) + (perturb)
+    const R fj = fma(itau, (even - odd) - f[j], f[j]) + pert;
+    const R fri = fma(wr, fi, kp);
+    const R frj = fma(wr, fj, -kp);
+    IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
+    IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
+    if (GHOSTS && nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
+      for (int k = 0; k < nimg; ++k) {
+        IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
+        IO::store(A.pout, A.g.nstore, j, si + dimg[k], frj, fj - frj, f0, ph);
+      }
     }
   }
   Fn_out = Fn;
+}
+
+// collide_store from the pulled, post-exchange pairs (the colour-blind sums are what it reads).
+template <int Q, int S>
+__device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nimg, const int (&dimg)[3],
+                                              const V2<typename Storage<S>::real> (&g)[Q],
+                                              typename Storage<S>::real rr,
+                                              typename Storage<S>::real rb,
+                                              typename Storage<S>::real irho,
+                                              const typename Storage<S>::real (&rnb)[Q],
+                                              typename Storage<S>::real& Fn_out) {
+  using R = typename Storage<S>::real;
+  R f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = g[i].r + g[i].b;
+  collide_store<Q, S, true>(A, si, nimg, dimg, f, rr, rb, irho, rnb, Fn_out);
 }
 
 // Ghost images of the column (a, b): storage deltas (plane-invariant).
@@ -361,20 +403,21 @@ __device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d
   return n;
 }
 
-// Per-cell tail of the fused step, called by step_tile for every fluid cell of the tile once its
-// pulled, post-exchange populations g and the neighbour phase field rnb are at hand: Eq.
+// Per-cell tail of the fused step, called by step_tile for every fluid cell of the tile once the
+// colour-blind sums f_i = g_i^r + g_i^b of its pulled, post-exchange populations (the exchange
+// keeps each f_i), rho_r, rho_b and the neighbour phase field rnb are at hand: Eq.
 // (collision) to Eq. (recolor) and the store, the site byte of this step and the ledger terms.
 struct StepEpilogue {
   template <int Q, int S, class R>
   __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
-                                       const int (&dimg)[3], const V2<R> (&g)[Q], R rr, R rb,
+                                       const int (&dimg)[3], const R (&f)[Q], R rr, R rb,
                                        R irho, R e, uint32_t flags, const R (&rnb)[Q],
                                        long long& n_sites, double& removed) const {
     R Fn;
-    collide_store<Q, S>(A, si, nimg, dimg, g, rr, rb, irho, rnb, Fn);
+    collide_store<Q, S, false>(A, si, nimg, dimg, f, rr, rb, irho, rnb, Fn);  // no ghosts
     uint32_t mb = flags;
     if (A.ph.rule == 0) {
-      const R d = Fn - (R)A.ph.threshold;
+      const R d = Fn - PHYS(R, A.ph, threshold);
       mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
     }
     A.mask_out[cell] = (uint8_t)mb;
@@ -395,10 +438,10 @@ struct TileSmem {
   static constexpr int HX = TX + 2, HY = L::D3 ? TH + 2 : 1;
   static constexpr bool DEV = Storage<S>::dev;
   static constexpr int RX = DEV ? TX + 4 : 1, RY = DEV ? (L::D3 ? TH + 4 : 1) : 1, RS = DEV ? 3 : 1;
-  // every part starts on a 16-byte boundary (the parking columns hold double2 in FP64)
+  // every part starts on a 16-byte boundary
   static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
   static constexpr int REST = ((RS * RY * RX * 8) + 15) & ~15;
-  static constexpr int PARK = ((CPT * Q * TX * TY * (int)(sizeof(R) == 8 ? 16 : 8)) + 15) & ~15;
+  static constexpr int PARK = ((CPT * Q * TX * TY * (int)sizeof(R)) + 15) & ~15;
   static constexpr int BYTES = RING + REST + PARK;
   static_assert(RING % 16 == 0 && REST % 16 == 0 && BYTES % 16 == 0, "16-byte aligned parts");
 };
@@ -520,10 +563,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   };
   auto restbox = [&](int slot, int y, int x) -> float2 { return rest_ring[slot][y][x]; };
 
-  // Pulled, post-exchange populations of the next plane wait in thread-private columns of
-  // shared memory (only this thread reads or writes its columns, so no barrier guards them).
-  using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
-  Vec* parked = reinterpret_cast<Vec*>(park_mem);  // [CPT][Q][NT]
+  // The colour-blind sums of the next plane's pulled, post-exchange populations wait in
+  // thread-private columns of shared memory (only this thread reads or writes its columns, so no
+  // barrier guards them).
+  R* parked = reinterpret_cast<R*>(park_mem);  // [CPT][Q][NT]
 
   struct CellScalars {
     R rr, rb, e, irho;
@@ -606,12 +649,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        Vec v;
-        v.x = g[c][i].r;
-        v.y = g[c][i].b;
-        parked[(c * Q + i) * NT + tid] = v;
-      }
+      for (int i = 0; i < Q; ++i) parked[(c * Q + i) * NT + tid] = g[c][i].r + g[c][i].b;
   }
   if (DEV) __syncthreads();  // the first fill below restages a rest slot the pulls above read
 
@@ -627,15 +665,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       // plane m of cell c leaves its parking column, plane m+1 takes its place
-      V2<R> own[Q];
+      R own[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const Vec v = parked[(c * Q + i) * NT + tid];
-        own[i] = {v.x, v.y};
-        Vec w;
-        w.x = g[c][i].r;
-        w.y = g[c][i].b;
-        parked[(c * Q + i) * NT + tid] = w;
+        own[i] = parked[(c * Q + i) * NT + tid];
+        parked[(c * Q + i) * NT + tid] = g[c][i].r + g[c][i].b;
       }
       if (!(active[c] && cur[c].ok)) continue;
       const int ly = ly0 + c * TY;

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
           collide_store<Q, S>(A, sidx(G, me.a, me.b, pc.m), nimg, dimg, g, rr, rb, irho, rnb, Fn);
           uint32_t mb = fl;
           if (A.ph.rule == 0) {
-            const R d = Fn - (R)A.ph.threshold;
+            const R d = Fn - PHYS(R, A.ph, threshold);
             mb |= (d > R(0) ? 2u : 0u) | (fabs(d) < R(1e-6) ? 8u : 0u);
           }
           A.mask_out[cell] = (uint8_t)mb;

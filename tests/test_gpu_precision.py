@@ -86,3 +86,18 @@ def test_one_step_matches_oracle_within_storage_rounding(storage, q, shape):
     assert rel_linf(g["rho_b"].cpu().numpy(), run.macros()["rho_b"]) <= tol
     far = run.margin > 1e-4
     assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, run.mask[far])
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+@pytest.mark.parametrize("q,shape,nvar", [(9, (1, 40, 130), 2), (19, (12, 21, 37), 5)])
+def test_every_variant_within_storage_rounding(storage, q, shape, nvar):
+    case = inputs.Case("variants", q, shape, R0=5.0, noise=1e-6, phi=1e-5, rho_r_in=2.0)
+    run = oracle_run(case, 3)
+    tol = 5e-4 if storage == "f16dev" else 5e-3
+    for v in range(nvar):
+        sim = gpu_sim(case, storage)
+        sim.tune(0, v)
+        sim.step(3)
+        g = sim.macros()
+        assert rel_linf(g["rho_r"].cpu().numpy(), run.macros()["rho_r"]) <= tol, v
+        assert rel_linf(g["rho_b"].cpu().numpy(), run.macros()["rho_b"]) <= tol, v
