@@ -202,7 +202,7 @@ struct AdjointEpilogue {
   __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, int si, int /*nimg*/,
                                        const int (&)[3], const R (&g)[Q], R rr, R rb, R irho,
                                        R /*e*/, uint32_t /*flags*/, const R (&rnb)[Q],
-                                       long long&, double&) const {
+                                       int&, R&) const {
     using Vec = typename Storage<S>::vec;
     const int ns = A.g.nstore;
     const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);

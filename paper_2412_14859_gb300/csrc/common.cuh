@@ -163,8 +163,10 @@ struct PopIO<S, Q, true> {
     const P* d = reinterpret_cast<const P*>(reinterpret_cast<const char*>(base) +
                                             dev_block_offset(nstore)) +
                  (size_t)(dir - 1) * nstore + si;
-    float2 v = Storage<S>::unpack(__ldg(d));
-    return {fmaf(f0.x, ph.kap_r[i], v.x * ph.inv_scale), fmaf(f0.y, ph.kap_b[i], v.y * ph.inv_scale)};
+    const float2 v = Storage<S>::unpack(__ldg(d));
+    const float2 r = __ffma2_rn(f0, make_float2(ph.kap_r[i], ph.kap_b[i]),
+                                __fmul2_rn(v, make_float2(ph.inv_scale, ph.inv_scale)));
+    return {r.x, r.y};
   }
   static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, float r,
                                                float b, V2<float> f0, const Physics& ph) {
@@ -174,7 +176,11 @@ struct PopIO<S, Q, true> {
     }
     P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(base) + dev_block_offset(nstore)) +
            (size_t)(i - 1) * nstore + si;
-    *d = Storage<S>::pack((r - f0.r * ph.kap_r[i]) * ph.scale, (b - f0.b * ph.kap_b[i]) * ph.scale);
+    // (f - f0 kappa) scale for both components in packed FP32
+    const float2 dev = __fmul2_rn(
+        __ffma2_rn(make_float2(-f0.r, -f0.b), make_float2(ph.kap_r[i], ph.kap_b[i]), make_float2(r, b)),
+        make_float2(ph.scale, ph.scale));
+    *d = Storage<S>::pack(dev.x, dev.y);
   }
 };
 

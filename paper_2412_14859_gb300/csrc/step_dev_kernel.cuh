@@ -54,7 +54,9 @@ __device__ __forceinline__ void dev_decode(const Physics& ph, const uint32_t (&r
     P pv;
     *reinterpret_cast<uint32_t*>(&pv) = raw[i];
     const float2 d = Storage<S>::unpack(pv);
-    g[i] = {fmaf(rs.x, ph.kap_r[i], d.x * ph.inv_scale), fmaf(rs.y, ph.kap_b[i], d.y * ph.inv_scale)};
+    const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
+                                __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
+    g[i] = {v.x, v.y};
   }
 }
 

@@ -27,8 +27,8 @@ KernelRef step_kernel_f32(int q, int variant) {
       case 0: return reg_ref<19, 16, 16, 2, 1>();
       case 1: return reg_ref<19, 32, 8, 3, 1>();
       case 2: return reg_ref<19, 32, 8, 2, 1>();
-      case 3: return reg_ref<19, 16, 16, 3, 1>();
-      case 4: return reg_ref<19, 32, 8, 2, 2>();
+      case 3: return reg_ref<19, 16, 16, 1, 2>();
+      case 4: return reg_ref<19, 32, 8, 1, 2>();
     }
   } else if (q == 9) {
     switch (variant) {

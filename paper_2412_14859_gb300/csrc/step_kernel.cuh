@@ -137,10 +137,18 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
     uint32_t& flags, typename Storage<S>::real& irho) {
   using R = typename Storage<S>::real;
   R sr = R(0), sb = R(0);
+  if constexpr (std::is_same<R, float>::value) {  // both components in packed FP32
+    float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    sr += g[i].r;
-    sb += g[i].b;
+    for (int i = 0; i < Q; ++i) acc = __fadd2_rn(acc, make_float2(g[i].r, g[i].b));
+    sr = acc.x;
+    sb = acc.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      sr += g[i].r;
+      sb += g[i].b;
+    }
   }
   irho = recip<R>(sr + sb);
   const R rn_pre = (sr - sb) * irho;
@@ -250,7 +258,9 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
     P pv;
     *reinterpret_cast<uint32_t*>(&pv) = raw[i];
     const float2 d = Storage<S>::unpack(pv);
-    g[i] = {fmaf(rs.x, ph.kap_r[i], d.x * ph.inv_scale), fmaf(rs.y, ph.kap_b[i], d.y * ph.inv_scale)};
+    const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
+                                __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
+    g[i] = {v.x, v.y};
   }
 }
 
@@ -359,10 +369,25 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     const R odd = R(3) * rwc[c] * cu;
     const R pert = fma(kw[c], pc * pc, -kc[c]);  // Eq. (perturb), even in c
     const R kp = kr[c] * pc;                     // Eq. (recolor) term, odd in c
-    const R fi = fma(itau, (even + odd) - f[i], f[i]) + pert;  // Eq. (collision) + (perturb)
-    const R fj = fma(itau, (even - odd) - f[j], f[j]) + pert;
-    const R fri = fma(wr, fi, kp);
-    const R frj = fma(wr, fj, -kp);
+    R fi, fj, fri, frj;
+    if constexpr (std::is_same<R, float>::value) {
+      // both directions of the pair in packed FP32 (same roundings as the scalar form)
+      const float2 fv = make_float2(f[i], f[j]);
+      const float2 m1 = make_float2(-1.0f, -1.0f);
+      const float2 feq = __fadd2_rn(make_float2(even, even), make_float2(odd, -odd));
+      float2 post = __ffma2_rn(make_float2(itau, itau), __ffma2_rn(fv, m1, feq), fv);
+      post = __fadd2_rn(post, make_float2(pert, pert));
+      const float2 fr = __ffma2_rn(make_float2(wr, wr), post, make_float2(kp, -kp));
+      fi = post.x;
+      fj = post.y;
+      fri = fr.x;
+      frj = fr.y;
+    } else {
+      fi = fma(itau, (even + odd) - f[i], f[i]) + pert;  // Eq. (collision) + (perturb)
+      fj = fma(itau, (even - odd) - f[j], f[j]) + pert;
+      fri = fma(wr, fi, kp);
+      frj = fma(wr, fj, -kp);
+    }
     IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
     IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
     if (GHOSTS && nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
@@ -412,7 +437,7 @@ struct StepEpilogue {
   __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
                                        const int (&dimg)[3], const R (&f)[Q], R rr, R rb,
                                        R irho, R e, uint32_t flags, const R (&rnb)[Q],
-                                       long long& n_sites, double& removed) const {
+                                       int& n_sites, R& removed) const {
     R Fn;
     collide_store<Q, S, false>(A, si, nimg, dimg, f, rr, rb, irho, rnb, Fn);  // no ghosts
     uint32_t mb = flags;
@@ -423,7 +448,7 @@ struct StepEpilogue {
     A.mask_out[cell] = (uint8_t)mb;
     if (flags & 1u) {
       ++n_sites;
-      removed += (double)e;
+      removed += e;
     }
   }
 };
@@ -576,8 +601,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   CellScalars cur[CPT], nxt[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), 0u, 0u, false};
-  n_sites = 0;
-  removed = 0.0;
+  // this thread's sites and removed mass (a sum over at most one cell column: the kernel's own
+  // real type suffices; the FP64 total is formed below and in the block reduction)
+  int nloc = 0;
+  R rem = R(0);
 
   // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
   // post-exchange populations are returned in g.
@@ -676,21 +703,29 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       const int s0 = (m - m0 + 1) & 3;
       const R ownrn = ring[s0][ly + OB][lx + 1];
       R rnb[Q];
+      if (cur[c].bits == 0) {  // no neighbour is solid or beyond a wall
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int s = (m - m0 + 1 + L::cm(i)) & 3;
-        const bool solid_nb = (cur[c].bits >> opp(i)) & 1u;  // x + c_i is the source of opp(i)
-        rnb[i] = solid_nb ? ownrn : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
+        for (int i = 0; i < Q; ++i)
+          rnb[i] = ring[(m - m0 + 1 + L::cm(i)) & 3][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const int s = (m - m0 + 1 + L::cm(i)) & 3;
+          const bool solid_nb = (cur[c].bits >> opp(i)) & 1u;  // x + c_i is the source of opp(i)
+          rnb[i] = solid_nb ? ownrn : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
+        }
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
       epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
                               cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
-                              n_sites, removed);
+                              nloc, rem);
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];
   }
-
+  n_sites = nloc;
+  // a scalar flux moves varphi at every site: n varphi in FP64, exact to one rounding
+  removed = A.ph.phi_field ? (double)rem : (double)nloc * A.ph.varphi;
 }
 
 // Block-wide sum of (n_sites, removed) into thread 0 (warp shuffles, then shared memory).
