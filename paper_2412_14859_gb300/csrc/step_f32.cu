@@ -24,11 +24,11 @@ static KernelRef reg_ref() {
 KernelRef step_kernel_f32(int q, int variant) {
   if (q == 19) {
     switch (variant) {
-      case 0: return reg_ref<19, 16, 16, 2, 1>();
-      case 1: return reg_ref<19, 32, 8, 3, 1>();
-      case 2: return reg_ref<19, 32, 8, 2, 1>();
-      case 3: return reg_ref<19, 16, 16, 1, 2>();
-      case 4: return reg_ref<19, 32, 8, 1, 2>();
+      case 0: return reg_ref<19, 32, 4, 4, 1>();  // 128 threads, four CTAs per SM
+      case 1: return reg_ref<19, 16, 8, 4, 1>();
+      case 2: return reg_ref<19, 16, 16, 2, 1>();
+      case 3: return reg_ref<19, 16, 4, 8, 1>();  // 64 threads, eight CTAs per SM
+      case 4: return reg_ref<19, 32, 8, 2, 1>();
     }
   } else if (q == 9) {
     switch (variant) {

@@ -24,11 +24,11 @@ static KernelRef reg_ref() {
 KernelRef step_kernel_f64(int q, int variant) {
   if (q == 19) {
     switch (variant) {
-      case 0: return reg_ref<19, 32, 8, 1, 1>();
+      case 0: return reg_ref<19, 16, 8, 2, 1>();
       case 1: return reg_ref<19, 32, 8, 1, 2>();
       case 2: return reg_ref<19, 16, 16, 1, 1>();
       case 3: return reg_ref<19, 32, 8, 2, 1>();
-      case 4: return reg_ref<19, 16, 16, 2, 1>();
+      case 4: return reg_ref<19, 32, 4, 2, 1>();
     }
   } else if (q == 9) {
     switch (variant) {

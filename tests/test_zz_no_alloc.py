@@ -93,7 +93,7 @@ def test_static_scratch_rejects_bad_arguments():
     assert lib.cgevap_step_static_scratch(p, 1e-5, a.data_ptr(), a.data_ptr(), n, m.data_ptr(),
                                           m.data_ptr(), led.data_ptr(), s) == -1
     # A lattice whose grid needs more CTAs than the static scratch holds (one plane of 4096 x 2048
-    # columns: 32768 tiles of the default 16x16 shape) is refused.  The buffers are full-size, so nothing could run out of bounds
+    # columns: 65536 tiles of the default 32x4 shape) is refused.  The buffers are full-size, so nothing could run out of bounds
     # even if the size check were missing.
     big = binding.Params.from_buffer_copy(sim.params)
     big.nx, big.ny, big.nz = 4096, 2048, 1
