@@ -233,7 +233,7 @@ struct AdjointEpilogue {
 };
 
 template <int Q, int S, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 1)
+__global__ void __launch_bounds__(TX* TY, 256 / (TX * TY))
     cg_adjoint_local_kernel(const __grid_constant__ StepArgs A,
                             const __grid_constant__ AdjointOut O) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];

@@ -31,8 +31,8 @@ inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) /
 }  // namespace
 
 KernelRef adjoint_local_kernel(int q, int storage) {
-  if (q == 19 && storage == ST_F64) return adj_ref<19, ST_F64, 32, 8>();
-  if (q == 19 && storage == ST_F32) return adj_ref<19, ST_F32, 32, 8>();
+  if (q == 19 && storage == ST_F64) return adj_ref<19, ST_F64, 32, 4>();
+  if (q == 19 && storage == ST_F32) return adj_ref<19, ST_F32, 32, 4>();
   if (q == 9 && storage == ST_F64) return adj_ref<9, ST_F64, 128, 1>();
   if (q == 9 && storage == ST_F32) return adj_ref<9, ST_F32, 128, 1>();
   return {nullptr, 0};

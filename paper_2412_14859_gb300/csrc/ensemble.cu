@@ -3,9 +3,10 @@
 // in a CUDA graph, with the tiling picked by a measuring autotuner.
 //
 // Work list.  A step of a member is split into items: (member, tile, chunk of planes) exactly as
-// the single-lattice step kernel splits it.  A D3Q19 item fills a 256-thread CTA (32 x 8 tile);
-// D2Q9 items are narrower and run G at a time in one CTA, one per group of 256/G threads (row
-// tiles of 256/G cells), with their barrier rounds padded to the longest chunk of the pack.
+// the single-lattice step kernel splits it.  A D3Q19 item fills a 128-thread CTA (32 x 4 tile;
+// four CTAs per SM, as the fastest single-lattice step); D2Q9 items are narrower and run G at a
+// time in one CTA, one per group of 128/G threads (row tiles of 128/G cells), with their barrier
+// rounds padded to the longest chunk of the pack.
 // CTAs take items (or packs) in a strided loop, meet at a grid barrier after every step, and fold
 // the per-item ledger partials of each member in item order (deterministic).  Every wait is
 // bounded; a barrier that gives up sets the status word, the CTAs finish their loops and the
@@ -77,9 +78,12 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status) {
   __syncthreads();
 }
 
+constexpr int kEnsThreads = 128;  // threads per CTA
+constexpr int kEnsTy = 4;         // D3Q19 item tile: 32 x kEnsTy columns
+
 template <int G>
-__global__ void __launch_bounds__(256, 1) cg_ensemble_kernel(const __grid_constant__ EnsArgs E) {
-  constexpr int NT = 256;
+__global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __grid_constant__ EnsArgs E) {
+  constexpr int NT = kEnsThreads;
   constexpr int GT = NT / G;  // threads per D2Q9 group
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double gsum_d[NT / 32];
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(256, 1) cg_ensemble_kernel(const __grid_consta
         A.pout = M.state[c ^ 1];
         A.mask_in = M.mask[c];
         A.mask_out = M.mask[c ^ 1];
-        step_tile<19, ST_F32, 32, 8, 1>(A, it.y, it.z, smem, n, d);
+        step_tile<19, ST_F32, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
         block_sum<NT>(n, d);
         if (tid == 0) {
           pr[w] = d;
@@ -182,9 +186,9 @@ __global__ void __launch_bounds__(256, 1) cg_ensemble_kernel(const __grid_consta
 // Resident CTAs of the ensemble kernel for group count G (0 on error), and its launcher.
 template <int G>
 static int ens_smem() {
-  return G * TileSmem<9, ST_F32, 256 / G, 1, 1>::BYTES > TileSmem<19, ST_F32, 32, 8, 1>::BYTES
-             ? G * TileSmem<9, ST_F32, 256 / G, 1, 1>::BYTES
-             : TileSmem<19, ST_F32, 32, 8, 1>::BYTES;
+  constexpr int b2 = G * TileSmem<9, ST_F32, kEnsThreads / G, 1, 1>::BYTES;
+  constexpr int b3 = TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES;
+  return b2 > b3 ? b2 : b3;
 }
 
 template <int G>
@@ -275,7 +279,7 @@ int build_plan(cgevap_ens* e) {
   std::vector<EnsMember> mem(e->n);
   std::vector<int4> it3, it2;
   std::vector<std::vector<int4>> per2(e->n), per3(e->n);
-  const int gt = 256 / e->groups;
+  const int gt = kEnsThreads / e->groups;
   for (int j = 0; j < e->n; ++j) {
     SimView v;
     if (sim_view(e->sims[j], &v) != CGEVAP_OK) return efail(e, CGEVAP_ERR_ARG, "bad member");
@@ -289,7 +293,7 @@ int build_plan(cgevap_ens* e) {
     M.mask[0] = v.mask[0];
     M.mask[1] = v.mask[1];
     M.ledger = v.ledger;
-    const int tx = M.q == 19 ? 32 : gt, ty = M.q == 19 ? 8 : 1;
+    const int tx = M.q == 19 ? 32 : gt, ty = M.q == 19 ? kEnsTy : 1;
     const int pc = M.q == 19 ? e->pc3 : e->pc2;
     M.a.ntx = (v.g.na + tx - 1) / tx;
     M.a.nty = (v.g.nb + ty - 1) / ty;
@@ -364,7 +368,7 @@ int build_plan(cgevap_ens* e) {
   e->smem = smem_for_groups(e->groups);
   EN_CUDA(e, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem));
   int occ = 0, sms = 0;
-  EN_CUDA(e, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, e->smem));
+  EN_CUDA(e, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kEnsThreads, e->smem));
   EN_CUDA(e, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
   if (occ < 1) return efail(e, CGEVAP_ERR_UNSUPPORTED, "ensemble kernel does not fit on an SM");
   e->grid = std::min(occ * sms, std::max(1, e->n3 + e->npack));
@@ -394,7 +398,7 @@ int launch(cgevap_ens* e, int nsteps) {
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(e->grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kEnsThreads);
   cfg.dynamicSmemBytes = e->smem;
   cfg.stream = e->stream;
   cudaLaunchAttribute attr[1];

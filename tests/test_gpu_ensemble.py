@@ -99,7 +99,11 @@ def test_tunings_agree_and_autotune_restores_state():
         init_member(sim, case)
     ref.set_tuning(4, 64, 64)
     ref.step(8)
-    for a, b in zip(ens.members, ref.members):
-        assert torch.equal(a.populations(torch.float32), b.populations(torch.float32))
+    # tile widths differ between the tilings (another instantiation of the step), so equality
+    # holds up to the rounding of contracted multiply-adds
+    for j, (a, b) in enumerate(zip(ens.members, ref.members)):
+        fa, fb = a.populations(torch.float64), b.populations(torch.float64)
+        err = float((fa - fb).abs().max() / fb.abs().max())
+        assert err <= 1e-6, (j, err)
     ens.close()
     ref.close()
