@@ -1,0 +1,86 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench times (the default
+kernel of each storage): the GPU advances the lattice, its state is read back, the GPU takes one
+more step, and the oracle computes that step one cell at a time (orc_step_cells) for a seeded
+sample of cells -- interface cells, cells of the first and last planes and random cells -- from
+the same state.
+
+- 192^3 drop (density ratio 10): FP64 (<= 1e-12), FP32 (<= 1e-5), FP16 deviations (the storage
+  rounding of the outputs, <= 2e-4 of the largest population);
+- 256 x 256 x 128 sessile cap with walls on z and a flux field: FP32 (<= 1e-5).
+
+Site decisions are compared wherever the GPU did not flag the decision value as lying within
+1e-6 of the threshold (bit 2 of the site byte).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from harness import oracle_params
+from paper_2412_14859_gb300 import inputs
+from paper_2412_14859_gb300.binding import Sim
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 2e-4}
+
+
+def sample_cells(rhoN, shape, n=2000, seed=inputs.SEED + 31):
+    """Half the sample from the interface band |rho^N| < 0.6, a quarter from the first and last
+    planes (walls, periodic seams), a quarter anywhere."""
+    g = inputs.rng(seed)
+    band = np.flatnonzero(np.abs(rhoN.ravel()) < 0.6)
+    nz, ny, nx = shape
+    plane = ny * nx
+    edge = np.concatenate([np.arange(plane), np.arange((nz - 1) * plane, nz * plane)])
+    picks = [g.choice(band, n // 2, replace=False), g.choice(edge, n // 4, replace=False),
+             g.choice(rhoN.size, n - n // 2 - n // 4, replace=False)]
+    return np.unique(np.concatenate(picks)).astype(np.int64)
+
+
+def run_case(case, storage, phi_field=None, warm=10):
+    dev = torch.device("cuda", 0)
+    sim = Sim.from_case(case, storage)
+    if phi_field is not None:
+        sim.set_flux(0.0, torch.from_numpy(phi_field).to(dev))
+    else:
+        sim.set_flux(case.phi)
+    nz = case.noise_array(np.float64)
+    sim.init_equilibrium(torch.from_numpy(case.phase()).to(dev),
+                         None if nz is None else torch.from_numpy(nz).to(dev))
+    sim.step(warm)
+    f_in = sim.populations(torch.float64).cpu().numpy()  # the state the next step starts from
+    sim.step(1)
+    f_out = sim.populations(torch.float64).cpu().numpy()
+    mask = sim.mask().cpu().numpy().ravel()
+    sim.close()
+    p = oracle_params(case, phi_field=phi_field)
+    rhoN = oracle.macros(p, f_in)["rhoN"]
+    cells = sample_cells(rhoN, case.shape)
+    want, _, om = oracle.step_cells(p, f_in, None, cells)
+    flat = f_out.reshape(2, case.q, -1)
+    got = np.stack([flat[:, :, c] for c in cells])  # [n, 2, Q]
+    return got, want, mask[cells], om
+
+
+def check(got, want, gm, om, tol):
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= tol, err
+    far = (gm & 4) == 0
+    assert np.array_equal((gm & 1)[far], om[far])
+    assert int(om.sum()) > 100  # the sample holds sites
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev"])
+def test_sphere_192_sampled_step(storage):
+    case = inputs.sphere_3d(192)
+    check(*run_case(case, storage), TOL[storage])
+
+
+def test_sessile_cap_full_box_sampled_step():
+    case = inputs.sessile_cap_3d()
+    nz, ny, nx = case.shape
+    basis = inputs.radial_basis(case.shape, ((ny - 1) / 2.0, (nx - 1) / 2.0), case.R0, 16)
+    a, _ = inputs.flux_fit_parameters(16)
+    phi = inputs.poly_flux(basis, case.phi, a)
+    check(*run_case(case, "f32", phi_field=phi), TOL["f32"])
