@@ -59,3 +59,41 @@ def test_evaporating_sphere_matches_paper_accuracy(case):
     # same scale: well under 1 % while R/R0 > 0.4, a few percent near R/R0 = 0.2
     assert errs[0] <= 0.5, errs
     assert errs[1] <= 5.0, errs
+
+
+def drop_radius_2d(sim, n):
+    rr = sim.macros()["rho_r"].cpu().numpy()[0]
+    half = 0.5 * rr.max()
+    lo, hi = n // 2 - 1, n // 2 + 1
+    out = []
+    for prof in (rr[lo:hi, :].mean(axis=0), rr[:, lo:hi].mean(axis=1)):
+        for idx in (np.arange(n // 2, n), np.arange(n // 2 - 1, -1, -1)):
+            p = prof[idx]
+            j = int(np.argmax(p < half))
+            out.append((j - 1) + (p[j - 1] - half) / (p[j - 1] - p[j]) + 0.5)
+    return float(np.mean(out)), float(rr.max())
+
+
+def test_radius_law_2d_band_rule():
+    """P7 on the D2Q9 256^2 drop (R0 = 40, phi = 1e-4, |rho^N| < 0.5) with S-bar = 1.697, the
+    band rule's value calibrated on the flat interface (tests/test_oracle_physics.py): the radius
+    follows R0 - (phi / rho_l) t to 2.2 % at R/R0 = 3/4 and 6.7 % at R/R0 = 1/2.  The error grows
+    with the curvature: a curved interface holds more band sites per unit length than a flat one,
+    the shape dependence of the site count that Sec. III discusses for its threshold."""
+    n = 256
+    c = inputs.Case("p7", 9, (1, n, n), R0=40.0, phi=1e-4, threshold=0.5, sbar=1.697)
+    sim = Sim.from_case(c, "f32")
+    sim.set_flux(0.0)
+    sim.init_equilibrium(torch.from_numpy(c.phase()).cuda())
+    sim.step(3000)
+    R0, rho0 = drop_radius_2d(sim, n)
+    sim.set_flux(c.phi)
+    t, errs = 0, []
+    for frac in (0.25, 0.5):
+        k = int(frac * R0 * rho0 / c.phi) - t
+        sim.step(k)
+        t += k
+        exact = 1.0 - t * c.phi / (R0 * rho0)
+        errs.append(abs(drop_radius_2d(sim, n)[0] / R0 - exact) / exact * 100.0)
+    assert errs[0] <= 3.0, errs
+    assert errs[1] <= 8.0, errs
