@@ -97,3 +97,65 @@ def test_radius_law_2d_band_rule():
         errs.append(abs(drop_radius_2d(sim, n)[0] / R0 - exact) / exact * 100.0)
     assert errs[0] <= 3.0, errs
     assert errs[1] <= 8.0, errs
+
+
+GOLDEN_E3 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hemisphere_e3.json")))
+
+
+def cap_height(sim, n):
+    """Distance from the wall z = -1/2 to the half-maximum crossing of rho_r along the wall
+    normal through the drop centre (profile averaged over the four central columns)."""
+    rr = sim.macros()["rho_r"].cpu().numpy()
+    half = 0.5 * rr.max()
+    lo, hi = n // 2 - 1, n // 2 + 1
+    p = rr[:, lo:hi, lo:hi].mean(axis=(1, 2))
+    j = int(np.argmax(p < half))
+    return float(0.5 + (j - 1) + (p[j - 1] - half) / (p[j - 1] - p[j]))
+
+
+@pytest.mark.parametrize("case", GOLDEN_E3["cases"], ids=lambda c: f"phi{c['phi']}")
+def test_evaporating_hemisphere_matches_paper(case):
+    n = 128
+    c = inputs.Case("hemisphere_e3", 19, (n, n, n), periodic=(1, 1, 0), geometry="cap",
+                    sigma=0.1, beta=0.99, site_rule=SITES_GRADIENT, threshold=0.305, sbar=3.0,
+                    phi=0.0, R0=44.0)
+    sim = Sim.from_case(c, "f32")
+    sim.set_flux(0.0)
+    sim.init_equilibrium(torch.from_numpy(c.phase()).cuda())
+    sim.step(3000)
+    h0 = cap_height(sim, n)
+    rho0 = float(sim.macros()["rho_r"].max())
+    te = h0 * rho0 / case["phi"]
+    sim.set_flux(case["phi"])
+    t = 0
+    for ts, paper in zip(case["t_star"], case["error_percent"]):
+        k = int(round(ts * te)) - t
+        sim.step(k)
+        t += k
+        exact = 1.0 - t / te
+        err = abs(cap_height(sim, n) / h0 - exact) / exact * 100.0
+        assert abs(err - paper) <= 1.0, (ts, err, paper)
+
+
+def test_sphere_256_size_independence():
+    """Sec. III.A.2 adds a 256^3 run with R0 = 88 to show that the same Gamma holds for a larger
+    drop: its errors stay at the 128^3 scale (measured 0.24 % and 1.2 % at t* = 0.54, 0.81)."""
+    n = 256
+    c = inputs.Case("sphere_e2_256", 19, (n, n, n), sigma=0.1, beta=0.99, site_rule=SITES_GRADIENT,
+                    threshold=0.305, sbar=3.0, phi=0.0, R0=88.0)
+    sim = Sim.from_case(c, "f32")
+    sim.set_flux(0.0)
+    sim.init_equilibrium(torch.from_numpy(c.phase()).cuda())
+    sim.step(3000)
+    R0 = sphere_radius(sim, n)
+    rho0 = float(sim.macros()["rho_r"].max())
+    te = R0 * rho0 / 0.03
+    sim.set_flux(0.03)
+    t, errs = 0, []
+    for ts in (0.54, 0.81):
+        k = int(round(ts * te)) - t
+        sim.step(k)
+        t += k
+        exact = 1.0 - t / te
+        errs.append(abs(sphere_radius(sim, n) / R0 - exact) / exact * 100.0)
+    assert errs[0] <= 0.5 and errs[1] <= 3.0, errs
