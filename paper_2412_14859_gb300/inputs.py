@@ -67,6 +67,33 @@ def sphere_phase(shape: Tuple[int, int, int], center, R0: float, width: float = 
     return np.tanh((R0 - r) / width)
 
 
+def cavity_solid(shape, r_in: float, r_out: float, depth: int) -> np.ndarray:
+    """A cylindrical cup on the wall z = -1/2: the ring r_in <= r < r_out (r the in-plane distance
+    from the box axis) of the first `depth` planes is solid."""
+    nz, ny, nx = shape
+    yy, xx = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    r = np.sqrt((yy - (ny - 1) / 2.0) ** 2 + (xx - (nx - 1) / 2.0) ** 2)
+    out = np.zeros(shape, np.uint8)
+    out[:depth] = ((r >= r_in) & (r < r_out)).astype(np.uint8)
+    return out
+
+
+def pinned_cap_phase(shape, r_in: float, r_out: float, depth: int, angle_deg: float,
+                     width: float = 2.0) -> np.ndarray:
+    """Liquid filling the cup (r < r_in below its rim) and a spherical cap on it whose edge sits
+    on the outer rim r_out at the given contact angle: sphere radius r_out / sin(angle), centre
+    -r_out / tan(angle) above the rim plane z = depth - 1/2; tanh profiles of the given width."""
+    nz, ny, nx = shape
+    th = np.deg2rad(angle_deg)
+    R = r_out / np.sin(th)
+    zc = depth - 0.5 - r_out / np.tan(th)
+    zz, yy, xx = np.meshgrid(*(np.arange(n, dtype=np.float64) for n in shape), indexing="ij")
+    r = np.sqrt((yy - (ny - 1) / 2.0) ** 2 + (xx - (nx - 1) / 2.0) ** 2)
+    cap = np.tanh((R - np.sqrt(r ** 2 + (zz - zc) ** 2)) / width)
+    cup = np.tanh((r_in - r) / width)
+    return np.where(zz < depth, cup, cap)
+
+
 def centred(shape) -> Tuple[float, float, float]:
     return tuple((n - 1) / 2.0 for n in shape)
 
@@ -134,7 +161,15 @@ class Case:
         if self.geometry == "cap":
             nz, ny, nx = self.shape
             return sphere_phase(self.shape, (-0.5, (ny - 1) / 2.0, (nx - 1) / 2.0), self.R0)
+        if self.geometry == "pinned":
+            return pinned_cap_phase(self.shape, **self.extra)
         raise ValueError(self.geometry)
+
+    def solid(self) -> Optional[np.ndarray]:
+        """Solid cells of the geometry (uint8 [nz, ny, nx]) or None."""
+        if self.geometry == "pinned":
+            return cavity_solid(self.shape, **{k: self.extra[k] for k in ("r_in", "r_out", "depth")})
+        return None
 
     def noise_array(self, dtype=np.float64) -> Optional[np.ndarray]:
         if self.noise == 0.0:
@@ -175,6 +210,16 @@ def sessile_cap_3d(shape=(128, 256, 256), R0: float = 48.0, phi0: float = 2e-5) 
     both ends of z, unit density ratio, A = 0.005, band threshold 0.5, FP32, 2000 steps."""
     return Case("sessile_cap_3d", 19, tuple(shape), periodic=(1, 1, 0), R0=R0, phi=phi0,
                 geometry="cap", steps=2000, sigma=sigma_from_amplitude(0.005))
+
+
+def pinned_cap_3d(n: int = 192, phi: float = 3e-3) -> Case:
+    """The pinned spherical cap of Sec. III.A.4: D3Q19 n^3, walls at both ends of z, a cylindrical
+    cup (inner radius 50, outer radius 53, depth 8) on the wall z = -1/2, a cap pinned on its outer
+    rim at about 120 degrees; unit density ratio, beta = 0.99, sigma = 0.1, Gamma = 0.305 with |F|
+    of the previous step, S-bar = 3."""
+    return Case("pinned_cap_3d", 19, (n, n, n), periodic=(1, 1, 0), sigma=0.1, beta=0.99,
+                site_rule=RULE_GRADIENT, threshold=0.305, sbar=3.0, phi=phi, geometry="pinned",
+                extra={"r_in": 50.0, "r_out": 53.0, "depth": 8, "angle_deg": 120.0})
 
 
 def flux_fit_parameters(K: int = 16, seed: int = SEED):

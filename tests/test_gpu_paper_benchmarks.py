@@ -159,3 +159,39 @@ def test_sphere_256_size_independence():
         exact = 1.0 - t / te
         errs.append(abs(sphere_radius(sim, n) / R0 - exact) / exact * 100.0)
     assert errs[0] <= 0.5 and errs[1] <= 3.0, errs
+
+
+GOLDEN_F4 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pinned_cap.json")))
+
+
+def test_pinned_cap_before_unpinning():
+    """The pinned cap of Sec. III.A.4 at phi = 3e-3 (tests/golden/pinned_cap.json): the height
+    law h0 - 2 phi t / rho0 holds as the paper finds at t* = 0.332 (measured 1.85 % against the
+    printed 2.5 %).  Later the contact line leaves the rim earlier than in the paper (pinning at a
+    sharp solid edge depends on how neutral wetting is discretised there), so the comparison
+    stops before unpinning."""
+    case = [c for c in GOLDEN_F4["cases"] if c["phi"] == 0.003][0]
+    c = inputs.pinned_cap_3d(192, case["phi"])
+    n, depth = 192, c.extra["depth"]
+    sim = Sim.from_case(c, "f32")
+    sim.set_solid(torch.from_numpy(c.solid()).cuda())
+    sim.set_flux(0.0)
+    sim.init_equilibrium(torch.from_numpy(c.phase()).cuda())
+    sim.step(6000)
+
+    def height():
+        rr = sim.macros()["rho_r"].cpu().numpy()
+        half = 0.5 * rr.max()
+        p = rr[:, n // 2 - 1:n // 2 + 1, n // 2 - 1:n // 2 + 1].mean(axis=(1, 2))
+        j = int(np.argmax(p < half))
+        return float((j - 1) + (p[j - 1] - half) / (p[j - 1] - p[j]) - (depth - 0.5)), float(rr.max())
+
+    h0, rho0 = height()
+    assert h0 == pytest.approx(91.6, abs=1.0)  # 120 degrees on the rim of radius 53
+    te = h0 * rho0 / (2 * case["phi"])
+    sim.set_flux(case["phi"])
+    t = int(round(case["t_star"] * te))
+    sim.step(t)
+    exact = 1.0 - t / te
+    err = abs(height()[0] / h0 - exact) / exact * 100.0
+    assert abs(err - case["error_percent"]) <= 1.5, err
