@@ -122,6 +122,24 @@ CGEVAP_API int cgevap_set_solid(cgevap_sim* sim, const uint8_t* dev_solid);
  * of red rest population per step (Eq. relation, Eq. exchange); negative phi condenses. */
 CGEVAP_API int cgevap_set_flux(cgevap_sim* sim, double phi, const void* dev_phi_field, int dtype);
 
+/* Heated-substrate flux (Sec. III.C, Eq. heated): a per-cell flux field
+ *   Phi(x) = phi_s / (K + h(x) / length),
+ * where h(x) is the liquid height of the column through x along the substrate normal (z in 3D,
+ * y in 2D): the sum of rho_r / (rho_r + rho_b) over the column's fluid cells, solid cells
+ * excluded.  `length` is the length scale R0 of h* = h / R0, K > 0 the kinetic constant.  The
+ * field is computed from the current state now, and again from the state before a step once
+ * `every` steps have passed since the last computation (every = 1: before every step); after
+ * cgevap_init_equilibrium / cgevap_set_populations the next step recomputes it.  Two kernels of
+ * fixed summation order compute it, so runs repeat bit for bit.  The mode stays on until
+ * cgevap_set_flux or cgevap_load replaces the flux.  Each site then moves Phi / S-bar (Eq.
+ * relation).  Errors: ARG (non-finite phi_s, K <= 0, length <= 0, every < 1, or a periodic
+ * substrate-normal axis), OOM, CUDA.  The adjoint entry points reject this mode (UNSUPPORTED). */
+CGEVAP_API int cgevap_set_flux_heated(cgevap_sim* sim, double phi_s, double K, double length, int every);
+
+/* The flux field the next step reads (FP64 [z][y][x] into dev_out; a scalar flux fills every
+ * cell with phi).  With a heated flux it is the field computed at the last recomputation. */
+CGEVAP_API int cgevap_get_flux_field(cgevap_sim* sim, double* dev_out);
+
 /* Initial state at rest: rho_r = rho_r_in (1 + rhoN0) / 2, rho_b = rho_b_in (1 - rhoN0) / 2,
  * f_i^k = rho_k phi_i(alpha_k) (Eq. feq with u = 0) plus dev_noise [k][i][z][y][x] if not NULL
  * (dtype noise_dtype).  dev_rhoN0 is FP64 [z][y][x].  Also resets the ledger and, for the

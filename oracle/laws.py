@@ -22,7 +22,8 @@ from scipy.integrate import solve_ivp
 def column_liquid_height(rho_r: np.ndarray, rho_b: np.ndarray, solid=None, axis: int = 0) -> np.ndarray:
     """Liquid height of every column along `axis` (the wall normal; axis 0 = z of a [z][y][x]
     field): the sum of rho_r / (rho_r + rho_b) over the column's fluid cells (reading R25)."""
-    frac = rho_r / (rho_r + rho_b)
+    with np.errstate(invalid="ignore", divide="ignore"):  # solid cells hold no mass
+        frac = rho_r / (rho_r + rho_b)
     if solid is not None:
         frac = np.where(np.asarray(solid) != 0, 0.0, frac)
     return frac.sum(axis=axis)
@@ -45,13 +46,20 @@ def heated_radius_rate(R: float, phi_s: float, K: float, R0: float, rho: float) 
 
 
 def heated_radius(t, phi_s: float, K: float, R0: float, rho: float, rtol: float = 1e-10) -> np.ndarray:
-    """R(t) of Eq. drrr from R(0) = R0, by an explicit Runge-Kutta 5(4) integration (App. C)."""
+    """R(t) of Eq. drrr from R(0) = R0, by an explicit Runge-Kutta 5(4) integration (App. C);
+    0 once the drop has gone (R reaches 1e-6 R0 in finite time)."""
     t = np.atleast_1d(np.asarray(t, np.float64))
+    gone = lambda _, y: y[0] - 1e-6 * R0
+    gone.terminal = True
     sol = solve_ivp(lambda _, y: [heated_radius_rate(y[0], phi_s, K, R0, rho)], (0.0, float(t.max())),
-                    [R0], method="RK45", t_eval=t, rtol=rtol, atol=1e-12 * R0)
-    if not sol.success:
+                    [R0], method="RK45", dense_output=True, events=gone, rtol=rtol, atol=1e-12 * R0)
+    if sol.status < 0:
         raise RuntimeError(sol.message)
-    return sol.y[0]
+    out = np.zeros_like(t)
+    live = t <= sol.t[-1]
+    if live.any():
+        out[live] = sol.sol(t[live])[0]
+    return out
 
 
 def constant_flux_length(t, L0: float, phi: float, rho: float):

@@ -59,6 +59,9 @@ _SIGS = {
     "cgevap_set_stream": (ctypes.c_int, [_vp, _vp]),
     "cgevap_set_solid": (ctypes.c_int, [_vp, _vp]),
     "cgevap_set_flux": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.c_int]),
+    "cgevap_set_flux_heated": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int]),
+    "cgevap_get_flux_field": (ctypes.c_int, [_vp, _vp]),
     "cgevap_init_equilibrium": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "cgevap_set_populations": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "cgevap_set_populations_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
@@ -206,6 +209,19 @@ class Sim:
         self._sync_stream()
         self._check(lib().cgevap_set_flux(self._h, float(phi), _ptr(field),
                                           _dt(field) if field is not None else 0))
+
+    def set_flux_heated(self, phi_s: float, K: float, length: float, every: int = 1):
+        """Heated-substrate flux phi_s / (K + h / length), h the liquid height of each cell's
+        column along the substrate normal, recomputed on the device every `every` steps."""
+        self._sync_stream()
+        self._check(lib().cgevap_set_flux_heated(self._h, float(phi_s), float(K), float(length), int(every)))
+
+    def flux_field(self) -> torch.Tensor:
+        """The flux field the next step reads, FP64, shape of the lattice (device)."""
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().cgevap_get_flux_field(self._h, out.data_ptr()))
+        return out
 
     def set_solid(self, solid: Optional[torch.Tensor]):
         self._sync_stream()

@@ -220,7 +220,21 @@ StepArgs cgevap::step_args(cgevap_sim* s) {
 
 namespace {
 
+// Recomputes the heated-substrate flux field from state[cur] (cgevap_set_flux_heated).
+int refresh_heated_flux(cgevap_sim* s) {
+  CG_CUDA(s, launch_heated_flux(aux_of(s), s->state[s->cur], s->heat.part, s->heat.phi_s, s->heat.K,
+                                s->heat.length, s->phi_field, s->p.storage == CGEVAP_F64 ? 1 : 0,
+                                s->stream));
+  s->heat.since = 0;
+  return CGEVAP_OK;
+}
+
 int launch_one_step(cgevap_sim* s) {
+  if (s->heat.on && s->heat.since >= s->heat.every) {
+    const int rc = refresh_heated_flux(s);
+    if (rc != CGEVAP_OK) return rc;
+  }
+  ++s->heat.since;
   StepArgs a = step_args(s);
   void* args[] = {&a, s->tmap[s->cur]};
   CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
@@ -251,7 +265,7 @@ void release(cgevap_sim* s) {
   void* ptrs[] = {s->state[0], s->state[1], s->mask[0],  s->mask[1],  s->links,
                   s->solid,    s->phi_field, s->ledger, s->part_removed, s->part_sites,
                   s->done,     s->tmp_rn,   s->flag,    s->staging, s->status,
-                  s->vol_part, s->vol_done};
+                  s->vol_part, s->vol_done, s->heat.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete s;
@@ -434,6 +448,7 @@ int cgevap_set_flux(cgevap_sim* s, double phi, const void* dev_phi_field, int dt
   if (!std::isfinite(phi)) return fail(s, CGEVAP_ERR_ARG, "phi is not finite");
   CG_CUDA(s, cudaSetDevice(s->device));
   s->phi = phi;
+  s->heat.on = 0;
   if (dev_phi_field) {
     if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
       return fail(s, CGEVAP_ERR_ARG, "flux dtype must be F64 or F32");
@@ -450,6 +465,44 @@ int cgevap_set_flux(cgevap_sim* s, double phi, const void* dev_phi_field, int dt
   return CGEVAP_OK;
 }
 
+int cgevap_set_flux_heated(cgevap_sim* s, double phi_s, double K, double length, int every) {
+  if (!s) return CGEVAP_ERR_ARG;
+  if (!std::isfinite(phi_s) || !(K > 0.0) || !std::isfinite(K) || !(length > 0.0) ||
+      !std::isfinite(length) || every < 1)
+    return fail(s, CGEVAP_ERR_ARG, "heated flux needs finite phi_s, K > 0, length > 0, every >= 1");
+  if (s->geom.per_m)
+    return fail(s, CGEVAP_ERR_ARG, "heated flux needs walls on the substrate normal (z in 3D, y in 2D)");
+  CG_CUDA(s, cudaSetDevice(s->device));
+  const HeatedPlan hp = heated_plan(s->geom);
+  if (!s->heat.part &&
+      cudaMalloc(&s->heat.part, (size_t)hp.nchunk * s->geom.na * s->geom.nb * sizeof(double)) != cudaSuccess)
+    return fail(s, CGEVAP_ERR_OOM, "cannot allocate the column partials");
+  const bool dbl = s->p.storage == CGEVAP_F64;
+  if (!s->phi_field && cudaMalloc(&s->phi_field, s->N * (dbl ? 8 : 4)) != cudaSuccess)
+    return fail(s, CGEVAP_ERR_OOM, "cannot allocate flux field");
+  s->phi = 0.0;
+  s->ph.varphi = 0.0;
+  s->ph.phi_field = s->phi_field;
+  s->heat.on = 1;
+  s->heat.phi_s = phi_s;
+  s->heat.K = K;
+  s->heat.length = length;
+  s->heat.every = every;
+  return refresh_heated_flux(s);
+}
+
+int cgevap_get_flux_field(cgevap_sim* s, double* dev_out) {
+  if (!s || !dev_out) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  if (s->ph.phi_field) {
+    CG_CUDA(s, launch_convert_field(s->phi_field, s->p.storage == CGEVAP_F64 ? CGEVAP_DTYPE_F64 : CGEVAP_DTYPE_F32,
+                                    dev_out, 1, s->N, s->stream));
+  } else {
+    CG_CUDA(s, launch_fill(dev_out, s->phi, s->N, s->stream));
+  }
+  return CGEVAP_OK;
+}
+
 int cgevap_init_equilibrium(cgevap_sim* s, const double* dev_rhoN0, const void* dev_noise,
                             int noise_dtype) {
   if (!s || !dev_rhoN0) return CGEVAP_ERR_ARG;
@@ -459,6 +512,7 @@ int cgevap_init_equilibrium(cgevap_sim* s, const double* dev_rhoN0, const void* 
   CG_CUDA(s, launch_init_equilibrium(aux_of(s), dev_rhoN0, dev_noise, noise_dtype,
                                      s->state[s->cur], s->stream));
   CG_CUDA(s, cudaMemsetAsync(s->ledger, 0, sizeof(DevLedger), s->stream));
+  s->heat.since = s->heat.every;  // a heated flux field follows the new state
   return refresh_gradient_sites(s);
 }
 
@@ -468,6 +522,7 @@ int cgevap_set_populations(cgevap_sim* s, const void* dev_f, int dtype) {
     return fail(s, CGEVAP_ERR_ARG, "dtype must be F64 or F32");
   CG_CUDA(s, cudaSetDevice(s->device));
   CG_CUDA(s, launch_set_populations(aux_of(s), dev_f, dtype, s->state[s->cur], s->stream));
+  s->heat.since = s->heat.every;
   return refresh_gradient_sites(s);
 }
 
@@ -661,6 +716,7 @@ int cgevap_load(cgevap_sim* s, const char* path) {
   }
   s->phi = phi;
   s->ph.varphi = phi / s->p.sbar;
+  s->heat.on = 0;  // a loaded field is held fixed
   if (has_field) {
     if (!s->phi_field && cudaMalloc(&s->phi_field, fbytes) != cudaSuccess)
       return fail(s, CGEVAP_ERR_OOM, "cannot allocate flux field");

@@ -1,6 +1,7 @@
 // aux_kernels.cu -- initial equilibrium, population import/export, macroscopic readout, the
-// gradient-rule sites of a given state, solid links and the health check.  One thread per cell;
-// none of these is on the timed path.
+// gradient-rule sites of a given state, solid links, the health check and the heated-substrate
+// flux field.  One thread per cell (per column for the flux field); none of these is on the
+// timed path of the constant-flux step.
 #include "launch.h"
 
 namespace cgevap {
@@ -276,9 +277,57 @@ __global__ void k_fill_ghosts(Geom g, void* state) {
   }
 }
 
+// Heated-substrate flux (Sec. III.C, Eq. heated), first pass: the liquid fraction
+// rho_r / (rho_r + rho_b) summed over the fluid cells of planes [y*cz, y*cz + cz) of every column
+// (a, b) along the march axis m (the wall normal), into part[chunk][column].  Threads run along a,
+// so every population plane is read coalesced.
+template <int Q, int S>
+__global__ void k_column_liquid(Geom g, Physics ph, const void* state, int cz, double* part) {
+  const int ncol = g.na * g.nb;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  const int m0 = blockIdx.y * cz;
+  const int m1 = min(g.nm, m0 + cz);
+  double h = 0.0;
+  for (int m = m0; m < m1; ++m) {
+    const int cell = m * ncol + col;
+    if (cell_solid(g, cell)) continue;
+    double fr[Q], fb[Q];
+    load_cell<Q, S>(state, g, cell, fr, fb, ph);
+    double rr = 0.0, rb = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rr += fr[i];
+      rb += fb[i];
+    }
+    if (rr + rb > 0.0) h += rr / (rr + rb);
+  }
+  part[(size_t)blockIdx.y * ncol + col] = h;
+}
+
+// Second pass: h of the column = the chunk partials summed in chunk order (deterministic), and
+// every cell of planes [y*cz, y*cz + cz) of the column takes phi_s / (K + h / length).
+__global__ void k_heated_field(Geom g, const double* part, int nchunk, int cz, double phi_s, double K,
+                               double inv_length, void* field, int field_double) {
+  const int ncol = g.na * g.nb;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  double h = 0.0;
+  for (int c = 0; c < nchunk; ++c) h += part[(size_t)c * ncol + col];
+  const double v = phi_s / (K + h * inv_length);
+  const int m0 = blockIdx.y * cz;
+  const int m1 = min(g.nm, m0 + cz);
+  for (int m = m0; m < m1; ++m) write_any(field, field_double ? 0 : 1, (size_t)m * ncol + col, v);
+}
+
 __global__ void k_convert(const void* in, int in_dt, void* out, int out_double, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     write_any(out, out_double ? 0 : 1, (size_t)i, read_any(in, in_dt, (size_t)i));
+}
+
+__global__ void k_fill(double* out, double v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = v;
 }
 
 }  // namespace
@@ -356,9 +405,36 @@ cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+HeatedPlan heated_plan(const Geom& g) {
+  HeatedPlan hp;
+  const int ncol = g.na * g.nb;
+  hp.col_blocks = (ncol + kThreads - 1) / kThreads;
+  int want = (152 * 16 + hp.col_blocks - 1) / hp.col_blocks;  // >= 16 CTAs per SM in all
+  if (want > g.nm) want = g.nm;
+  if (want < 1) want = 1;
+  hp.cz = (g.nm + want - 1) / want;
+  hp.nchunk = (g.nm + hp.cz - 1) / hp.cz;
+  return hp;
+}
+
+cudaError_t launch_heated_flux(const AuxArgs& a, const void* state, double* part, double phi_s,
+                               double K, double length, void* field, int field_double, cudaStream_t s) {
+  const HeatedPlan hp = heated_plan(a.g);
+  const dim3 grid((unsigned)hp.col_blocks, (unsigned)hp.nchunk);
+  CGEVAP_DISPATCH(a, k_column_liquid, grid, s, a.g, a.ph, state, hp.cz, part);
+  k_heated_field<<<grid, kThreads, 0, s>>>(a.g, part, hp.nchunk, hp.cz, phi_s, K, 1.0 / length, field,
+                                           field_double);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s) {
   k_convert<<<grid_for(n), kThreads, 0, s>>>(in, in_dtype, out, out_is_double, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* out, double v, long long n, cudaStream_t s) {
+  k_fill<<<grid_for(n), kThreads, 0, s>>>(out, v, n);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,18 @@ cudaError_t launch_health(const AuxArgs& a, const void* state, int* flag, cudaSt
 cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s);
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s);
+cudaError_t launch_fill(double* out, double v, long long n, cudaStream_t s);
+
+// Heated-substrate flux field (aux_kernels.cu; Sec. III.C, Eq. heated): every cell of a column
+// along the march axis (the wall normal) takes phi_s / (K + h / length), h = the column's summed
+// liquid fraction.  `part` holds heated_plan(g).nchunk * na * nb doubles; field is double
+// (field_double = 1) or float, [N].
+struct HeatedPlan {
+  int col_blocks = 1, cz = 1, nchunk = 1;
+};
+HeatedPlan heated_plan(const Geom& g);
+cudaError_t launch_heated_flux(const AuxArgs& a, const void* state, double* part, double phi_s,
+                               double K, double length, void* field, int field_double, cudaStream_t s);
 
 // Adjoint sweep (adjoint_kernels.cu).  The local kernel (kernel A) takes (StepArgs, AdjointOut)
 // and runs on the step's tile grid; F64 / F32 storage only.

@@ -47,6 +47,14 @@ struct cgevap_sim {
   cgevap::AdjointTape* tape = nullptr;  // checkpoints of cgevap_adjoint_forward (adjoint.cu)
   double* vol_part = nullptr;           // cgevap_volume scratch: kVolumeBlocks partials
   unsigned int* vol_done = nullptr;     // and its arrival counter
+  // heated-substrate flux (cgevap_set_flux_heated): phi_field is recomputed from the state before
+  // a step once `since` reaches `every`; part holds the column partials of launch_heated_flux
+  struct Heated {
+    int on = 0;
+    double phi_s = 0.0, K = 1.0, length = 1.0;
+    int every = 1, since = 0;
+    double* part = nullptr;
+  } heat;
   std::string err;
 };
 
