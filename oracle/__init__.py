@@ -56,6 +56,7 @@ class _Params(ctypes.Structure):
         ("phi_field", ctypes.POINTER(ctypes.c_double)),
         ("solid", ctypes.POINTER(ctypes.c_ubyte)),
         ("mask_given", ctypes.POINTER(ctypes.c_ubyte)),
+        ("outlet_rho_lo", ctypes.c_double), ("outlet_rho_hi", ctypes.c_double),
     ]
 
 
@@ -88,6 +89,7 @@ def _L():
         _lib.orc_step_cells.argtypes = [pp, dp, dp, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.c_longlong, dp, dp, up]
         _lib.orc_macros.argtypes = [pp, dp, dp, dp, dp, dp]
+        _lib.orc_outlet_blue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
     return _lib
 
 
@@ -126,6 +128,7 @@ class Params:
     phi_field: Optional[np.ndarray] = None
     solid: Optional[np.ndarray] = None
     mask_given: Optional[np.ndarray] = None
+    outlet_rho: Sequence[float] = (0.0, 0.0)  # blue outlets on the wall-normal axis (lo, hi); <= 0 wall
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -145,6 +148,7 @@ class Params:
             self.q, self.nx, self.ny, self.nz, (ctypes.c_int * 3)(*self.periodic),
             self.rho_r_in, self.rho_b_in, self.tau_r, self.tau_b, self.sigma, self.beta,
             self.site_rule, self.threshold, self.sbar, self.phi, _dp(pf), _up(sd), _up(mg),
+            float(self.outlet_rho[0]), float(self.outlet_rho[1]),
         )
 
 
@@ -201,6 +205,14 @@ def gradient_norm(p: Params, f: np.ndarray) -> np.ndarray:
     cp = p._c()
     _check(_L().orc_gradient_norm(ctypes.byref(cp), _dp(np.ascontiguousarray(f)), _dp(G)))
     return G
+
+
+def outlet_blue(q: int, inward: int, rho0: float, gb: np.ndarray) -> np.ndarray:
+    """The blue outlet (Sec. III.B.2) applied to one cell's pulled blue populations gb [Q] on
+    the first (inward = +1) or last (inward = -1) plane of the wall-normal axis."""
+    g = np.ascontiguousarray(gb, np.float64).copy()
+    _check(_L().orc_outlet_blue(q, inward, rho0, _dp(g)))
+    return g
 
 
 def macros(p: Params, f: np.ndarray):

@@ -147,8 +147,12 @@ void orc_perturbation_shape(int q, const double *F, double *out) {
 
 /* ---------------------------------------------------------------- geometry -------------- */
 
+/* The wall-normal axis of the outlets: z in 3D, y in 2D. */
+static int normal_axis(const orc_params *p) { return p->q == 19 ? 2 : 1; }
+
 static int valid_params(const orc_params *p) {
   if (!p) return 0;
+  if ((p->outlet_rho_lo > 0.0 || p->outlet_rho_hi > 0.0) && p->periodic[normal_axis(p)]) return 0;
   if (p->q != 9 && p->q != 19) return 0;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return 0;
   if (p->q == 9 && p->nz != 1) return 0;
@@ -186,6 +190,39 @@ static long long neighbour(const orc_params *p, int x, int y, int z, int dx, int
 
 /* Eq. (Stream) in pull form: f_i^k(x) = f_i^{k*}(x - c_i); where x - c_i is solid the
  * population leaving x towards it comes back reversed (halfway bounce-back). */
+/* Pressure outlet for the blue component (Sec. III.B.2; the boundary condition of Zou and He).
+ * gb holds the blue populations of a cell on an outlet plane after the pull, n the inward
+ * normal along `axis`.  The populations with c.n = +1 come from outside and are unknown; with
+ * the blue density fixed at rho0 and no blue velocity along the plane:
+ *   mass + normal momentum:  rho0 u_n = rho0 - (S_0 + 2 S_out),
+ *       S_0 = sum over c.n = 0, S_out = sum over c.n = -1 (known populations);
+ *   non-equilibrium bounce-back: g_i = g_opp(i) + (f_i^eq - f_opp(i)^eq) = g_opp(i) + 6 W_i rho0 u_n
+ *       (only the odd part of Eq. feq differs between i and opp(i));
+ *   tangential momentum zero: each tangential axis t gets -c_it N_t,
+ *       N_t = (1/2) sum over c.n = 0 of g_j c_jt.
+ * Red populations keep their bounce-back values: the outlet lets no red through. */
+static void outlet_blue(const lattice *L, int axis, int inward, double rho0, double gb[QMAX]) {
+  double s0 = 0.0, sout = 0.0, t[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < L->Q; i++) {
+    int cn = L->c[i][axis] * inward;
+    if (cn == 0) {
+      s0 += gb[i];
+      for (int d = 0; d < 3; d++)
+        if (d != axis) t[d] += L->c[i][d] * gb[i];
+    } else if (cn < 0) {
+      sout += gb[i];
+    }
+  }
+  double un = 1.0 - (s0 + 2.0 * sout) / rho0;
+  for (int i = 0; i < L->Q; i++) {
+    if (L->c[i][axis] * inward <= 0) continue;
+    double corr = 0.0;
+    for (int d = 0; d < 3; d++)
+      if (d != axis) corr += L->c[i][d] * 0.5 * t[d];
+    gb[i] = gb[L->opp[i]] + 6.0 * L->w[i] * rho0 * un - corr;
+  }
+}
+
 static void pull_cell(const orc_params *p, const lattice *L, const double *f_in, int x, int y,
                       int z, double g[2][QMAX]) {
   long long N = ncells(p), X = idx(p, x, y, z);
@@ -198,6 +235,10 @@ static void pull_cell(const orc_params *p, const lattice *L, const double *f_in,
         g[k][i] = f_in[((long long)k * L->Q + i) * N + S];
     }
   }
+  int ax = normal_axis(p);
+  int r[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
+  if (p->outlet_rho_lo > 0.0 && r[ax] == 0) outlet_blue(L, ax, +1, p->outlet_rho_lo, g[1]);
+  if (p->outlet_rho_hi > 0.0 && r[ax] == n[ax] - 1) outlet_blue(L, ax, -1, p->outlet_rho_hi, g[1]);
 }
 
 static void densities(const lattice *L, double g[2][QMAX], double *rr, double *rb) {
@@ -524,6 +565,16 @@ int orc_step_cells(const orc_params *p, const double *f_in, const double *G_prev
       for (int i = 0; i < Q; i++) o[k * Q + i] = out[k][i];
     out_G[s] = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
   }
+  return 0;
+}
+
+int orc_outlet_blue(int q, int inward, double rho0, double *gb) {
+  lattice L;
+  if (!make_lattice(q, &L) || (inward != 1 && inward != -1) || !(rho0 > 0.0)) return -1;
+  double g[QMAX];
+  for (int i = 0; i < L.Q; i++) g[i] = gb[i];
+  outlet_blue(&L, q == 19 ? 2 : 1, inward, rho0, g);
+  for (int i = 0; i < L.Q; i++) gb[i] = g[i];
   return 0;
 }
 

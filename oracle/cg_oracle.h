@@ -38,6 +38,9 @@ typedef struct {
   const double *phi_field;        /* per-cell flux [z][y][x] or NULL                            */
   const unsigned char *solid;     /* per-cell solid flag [z][y][x] or NULL                      */
   const unsigned char *mask_given; /* ORC_RULE_GIVEN: sites are the cells whose bit 0 is set     */
+  /* Blue pressure outlets (Sec. III.B.2) on the first / last plane of the wall-normal axis (z in
+   * 3D, y in 2D, which must have walls): the prescribed blue density there, or <= 0 for a wall. */
+  double outlet_rho_lo, outlet_rho_hi;
 } orc_params;
 
 typedef struct {
@@ -78,6 +81,11 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out, const doubl
 int orc_step_cells(const orc_params *p, const double *f_in, const double *G_prev,
                    const long long *cells, long long ncells, double *out_f, double *out_G,
                    unsigned char *out_mask);
+
+/* The blue outlet of one cell on its own: gb [Q] are the pulled blue populations of a cell on
+ * the first (inward = +1) or last (inward = -1) plane of the wall-normal axis; the populations
+ * entering from outside are replaced as the step does for an outlet of blue density rho0. */
+int orc_outlet_blue(int q, int inward, double rho0, double *gb);
 
 /* Local macroscopic fields of the state: rho_r, rho_b, u (3 x N) and rho^N. */
 int orc_macros(const orc_params *p, const double *f, double *rho_r, double *rho_b, double *u,
