@@ -136,6 +136,18 @@ CGEVAP_API int cgevap_set_flux(cgevap_sim* sim, double phi, const void* dev_phi_
  * substrate-normal axis), OOM, CUDA.  The adjoint entry points reject this mode (UNSUPPORTED). */
 CGEVAP_API int cgevap_set_flux_heated(cgevap_sim* sim, double phi_s, double K, double length, int every);
 
+/* Blue pressure outlets for density-contrast runs (Sec. III.B.2; the boundary condition of Zou
+ * and He) on the first (rho_lo) and last (rho_hi) plane of the wall-normal axis -- z in 3D, y in
+ * 2D, which must have walls.  A density <= 0 leaves that end a halfway bounce-back wall (the
+ * default).  Before every step, at each fluid cell of an outlet plane, the blue populations that
+ * enter from outside are rebuilt from the cell's known pulled ones so that the blue density is
+ * the given one and the blue velocity along the plane is zero (mass and normal momentum balance,
+ * bounce-back of the normal non-equilibrium part); red keeps the bounce-back (no red passes).
+ * The setting persists across cgevap_init_equilibrium, cgevap_set_populations and cgevap_load and
+ * is not written by cgevap_save.  Errors: ARG (non-finite density, a periodic wall-normal axis,
+ * two outlets on a single plane).  The adjoint entry points reject it (UNSUPPORTED). */
+CGEVAP_API int cgevap_set_outlets(cgevap_sim* sim, double rho_lo, double rho_hi);
+
 /* The flux field the next step reads (FP64 [z][y][x] into dev_out; a scalar flux fills every
  * cell with phi).  With a heated flux it is the field computed at the last recomputation. */
 CGEVAP_API int cgevap_get_flux_field(cgevap_sim* sim, double* dev_out);

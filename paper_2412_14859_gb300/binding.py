@@ -62,6 +62,7 @@ _SIGS = {
     "cgevap_set_flux_heated": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int]),
     "cgevap_get_flux_field": (ctypes.c_int, [_vp, _vp]),
+    "cgevap_set_outlets": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "cgevap_init_equilibrium": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "cgevap_set_populations": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "cgevap_set_populations_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
@@ -215,6 +216,10 @@ class Sim:
         column along the substrate normal, recomputed on the device every `every` steps."""
         self._sync_stream()
         self._check(lib().cgevap_set_flux_heated(self._h, float(phi_s), float(K), float(length), int(every)))
+
+    def set_outlets(self, rho_lo: float, rho_hi: float):
+        """Blue pressure outlets on the first / last plane of the wall-normal axis (<= 0: wall)."""
+        self._check(lib().cgevap_set_outlets(self._h, float(rho_lo), float(rho_hi)))
 
     def flux_field(self) -> torch.Tensor:
         """The flux field the next step reads, FP64, shape of the lattice (device)."""

@@ -172,6 +172,8 @@ int cgevap_adjoint_forward(cgevap_sim* s, int nsteps, int ckpt_every, double* de
     return sim_fail(s, CGEVAP_ERR_UNSUPPORTED, "the adjoint needs F64 or F32 storage");
   if (s->family != 0)
     return sim_fail(s, CGEVAP_ERR_UNSUPPORTED, "the adjoint needs the register-pipelined step (cgevap_tune family 0)");
+  if (s->outlet_rho[0] > 0.0 || s->outlet_rho[1] > 0.0)
+    return sim_fail(s, CGEVAP_ERR_UNSUPPORTED, "the adjoint does not differentiate the outlets (cgevap_set_outlets)");
   if (s->heat.on)
     return sim_fail(s, CGEVAP_ERR_UNSUPPORTED, "the adjoint needs a flux that does not depend on the state (heated flux set)");
   CG_CUDA(s, cudaSetDevice(s->device));

@@ -235,6 +235,8 @@ int launch_one_step(cgevap_sim* s) {
     if (rc != CGEVAP_OK) return rc;
   }
   ++s->heat.since;
+  if (s->outlet_rho[0] > 0.0 || s->outlet_rho[1] > 0.0)
+    CG_CUDA(s, launch_outlets(aux_of(s), s->state[s->cur], s->outlet_rho[0], s->outlet_rho[1], s->stream));
   StepArgs a = step_args(s);
   void* args[] = {&a, s->tmap[s->cur]};
   CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
@@ -489,6 +491,20 @@ int cgevap_set_flux_heated(cgevap_sim* s, double phi_s, double K, double length,
   s->heat.length = length;
   s->heat.every = every;
   return refresh_heated_flux(s);
+}
+
+int cgevap_set_outlets(cgevap_sim* s, double rho_lo, double rho_hi) {
+  if (!s) return CGEVAP_ERR_ARG;
+  if (!std::isfinite(rho_lo) || !std::isfinite(rho_hi))
+    return fail(s, CGEVAP_ERR_ARG, "outlet densities must be finite");
+  const bool lo = rho_lo > 0.0, hi = rho_hi > 0.0;
+  if ((lo || hi) && s->geom.per_m)
+    return fail(s, CGEVAP_ERR_ARG, "outlets need walls on the wall-normal axis (z in 3D, y in 2D)");
+  if (lo && hi && s->geom.nm < 2)
+    return fail(s, CGEVAP_ERR_ARG, "two outlets need at least two planes");
+  s->outlet_rho[0] = lo ? rho_lo : 0.0;
+  s->outlet_rho[1] = hi ? rho_hi : 0.0;
+  return CGEVAP_OK;
 }
 
 int cgevap_get_flux_field(cgevap_sim* s, double* dev_out) {

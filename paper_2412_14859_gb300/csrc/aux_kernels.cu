@@ -280,27 +280,29 @@ __global__ void k_fill_ghosts(Geom g, void* state) {
 // Heated-substrate flux (Sec. III.C, Eq. heated), first pass: the liquid fraction
 // rho_r / (rho_r + rho_b) summed over the fluid cells of planes [y*cz, y*cz + cz) of every column
 // (a, b) along the march axis m (the wall normal), into part[chunk][column].  Threads run along a,
-// so every population plane is read coalesced.
+// so every population plane is read coalesced.  The cell's densities are summed in the storage's
+// arithmetic (FP32 for FP32 and 16-bit storage, as in the step), the column in FP64.
 template <int Q, int S>
 __global__ void k_column_liquid(Geom g, Physics ph, const void* state, int cz, double* part) {
+  using R = typename Storage<S>::real;
   const int ncol = g.na * g.nb;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= ncol) return;
+  const int a = col % g.na, b = col / g.na;
   const int m0 = blockIdx.y * cz;
   const int m1 = min(g.nm, m0 + cz);
   double h = 0.0;
   for (int m = m0; m < m1; ++m) {
-    const int cell = m * ncol + col;
-    if (cell_solid(g, cell)) continue;
-    double fr[Q], fb[Q];
-    load_cell<Q, S>(state, g, cell, fr, fb, ph);
-    double rr = 0.0, rb = 0.0;
+    if (cell_solid(g, m * ncol + col)) continue;
+    const int si = sidx(g, a, b, m);
+    R rr = 0, rb = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      rr += fr[i];
-      rb += fb[i];
+      const auto v = PopIO<S, Q>::load(state, g.nstore, i, i, si, ph);
+      rr += v.r;
+      rb += v.b;
     }
-    if (rr + rb > 0.0) h += rr / (rr + rb);
+    if (rr + rb > R(0)) h += (double)(rr / (rr + rb));
   }
   part[(size_t)blockIdx.y * ncol + col] = h;
 }
@@ -323,6 +325,89 @@ __global__ void k_heated_field(Geom g, const double* part, int nchunk, int cz, d
 __global__ void k_convert(const void* in, int in_dt, void* out, int out_double, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     write_any(out, out_double ? 0 : 1, (size_t)i, read_any(in, in_dt, (size_t)i));
+}
+
+// Writes the blue half of the population pair of direction `dir` (>= 1) at storage index si,
+// leaving the red half's stored bits as they are.
+template <int S>
+__device__ __forceinline__ void store_blue(void* state, const Geom& g, const Physics& ph, int dir,
+                                           int si, double v) {
+  if constexpr (Storage<S>::dev) {
+    using P = typename Storage<S>::packed;
+    const float f0b = reinterpret_cast<const float2*>(state)[si].y;
+    P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(state) + dev_block_offset(g.nstore)) +
+           (size_t)(dir - 1) * g.nstore + si;
+    const float dv = __fmul_rn(__fmaf_rn(-f0b, ph.kap_b[dir], (float)v), ph.scale);
+    P w = *d;
+    w.y = Storage<S>::pack(0.0f, dv).y;
+    *d = w;
+  } else {
+    using Vec = typename Storage<S>::vec;
+    reinterpret_cast<Vec*>(state)[(size_t)dir * g.nstore + si].y = (typename Storage<S>::real)v;
+  }
+}
+
+// Blue pressure outlet (Sec. III.B.2, the boundary condition of Zou and He), run before a step on
+// the first (inward normal +m) and last (-m) plane of the march axis where a density is given.
+// The step pulls the populations entering through the plane from beyond the wall, i.e. by
+// halfway bounce-back from the cell's own slots of the opposite (leaving) directions.  This
+// kernel rebuilds the blue ones from the cell's pulled known populations -- blue density rho0,
+// no blue velocity along the plane:
+//   rho0 u_n = rho0 - (S_0 + 2 S_out)        (mass and normal momentum; S over c.n = 0 / -1),
+//   g_i = g_opp(i) + 6 W_i rho0 u_n - sum_t c_it N_t,   N_t = 1/2 sum_{c.n = 0} g_j c_jt
+// (non-equilibrium bounce-back: only the odd part of Eq. feq differs between i and opp(i)) --
+// and stores them in those leaving slots, so the step's bounce-back delivers them.  Red keeps
+// its bounce-back: the outlet is a wall for red.  Leaving slots of a plane are read by no other
+// cell, so the plane's cells are independent.
+template <int Q, int S>
+__global__ void k_outlet(Geom g, Physics ph, void* state, double rho_lo, double rho_hi) {
+  using L = Lattice<Q>;
+  const int ncol = g.na * g.nb;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * ncol; t += gridDim.x * blockDim.x) {
+    const int side = t / ncol;
+    const double rho0 = side ? rho_hi : rho_lo;
+    if (!(rho0 > 0.0)) continue;
+    const int col = t - side * ncol;
+    Coord c;
+    c.a = col % g.na;
+    c.b = col / g.na;
+    c.m = side ? g.nm - 1 : 0;
+    if (cell_solid(g, c.m * ncol + col)) continue;
+    const int inward = side ? -1 : 1;
+    const int si = sidx(g, c.a, c.b, c.m);
+    double gb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      int src = neighbour(g, c, -L::ca(i), -L::cb(i), -L::cm(i));
+      if (src >= 0 && cell_solid(g, src)) src = -1;
+      if (src < 0) {
+        gb[i] = (double)PopIO<S, Q>::load(state, g.nstore, i, opp(i), si, ph).b;
+      } else {
+        const Coord sc = coord_of(g, src);
+        gb[i] = (double)PopIO<S, Q>::load(state, g.nstore, i, i, sidx(g, sc.a, sc.b, sc.m), ph).b;
+      }
+    }
+    double s0 = 0.0, sout = 0.0, ta = 0.0, tb = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cn = L::cm(i) * inward;
+      if (cn == 0) {
+        s0 += gb[i];
+        ta += L::ca(i) * gb[i];
+        tb += L::cb(i) * gb[i];
+      } else if (cn < 0) {
+        sout += gb[i];
+      }
+    }
+    const double un = 1.0 - (s0 + 2.0 * sout) / rho0;
+    const Images im = images_of(g, c.a, c.b, c.m);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (L::cm(i) * inward <= 0) continue;
+      const double v = gb[opp(i)] + 6.0 * L::W(i) * rho0 * un - (L::ca(i) * 0.5 * ta + L::cb(i) * 0.5 * tb);
+      for (int j = 0; j < im.n; ++j) store_blue<S>(state, g, ph, opp(i), im.s[j], v);
+    }
+  }
 }
 
 __global__ void k_fill(double* out, double v, long long n) {
@@ -430,6 +515,11 @@ cudaError_t launch_heated_flux(const AuxArgs& a, const void* state, double* part
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s) {
   k_convert<<<grid_for(n), kThreads, 0, s>>>(in, in_dtype, out, out_is_double, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outlets(const AuxArgs& a, void* state, double rho_lo, double rho_hi, cudaStream_t s) {
+  CGEVAP_DISPATCH(a, k_outlet, grid_for(2LL * a.g.na * a.g.nb), s, a.g, a.ph, state, rho_lo, rho_hi);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,9 @@ cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s);
 cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int out_is_double,
                                  long long n, cudaStream_t s);
 cudaError_t launch_fill(double* out, double v, long long n, cudaStream_t s);
+// Blue pressure outlets (aux_kernels.cu; Sec. III.B.2) on the first / last plane of the march
+// axis, prescribed blue density rho_lo / rho_hi (<= 0: wall), written into state before a step.
+cudaError_t launch_outlets(const AuxArgs& a, void* state, double rho_lo, double rho_hi, cudaStream_t s);
 
 // Heated-substrate flux field (aux_kernels.cu; Sec. III.C, Eq. heated): every cell of a column
 // along the march axis (the wall normal) takes phi_s / (K + h / length), h = the column's summed

@@ -55,6 +55,7 @@ struct cgevap_sim {
     int every = 1, since = 0;
     double* part = nullptr;
   } heat;
+  double outlet_rho[2] = {0.0, 0.0};  // blue pressure outlets (cgevap_set_outlets); <= 0: wall
   std::string err;
 };
 
