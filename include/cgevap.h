@@ -62,6 +62,11 @@ extern "C" {
 #define CGEVAP_F32 1      /* FP32 storage, FP32 arithmetic                                     */
 #define CGEVAP_F16DEV 2   /* FP32 rest populations + FP16 deviations of the moving ones, FP32 */
 #define CGEVAP_BF16DEV 3  /* as F16DEV with BF16 deviations                                    */
+#define CGEVAP_F32RC 4    /* "recolour on pull": per cell the Q colour-blind post-collision
+                             populations and one record (rho_r / rho, V) in FP32, from which the
+                             next step forms each colour as Eq. (recolor) does; Q + 4 floats per
+                             cell instead of 2Q, FP32 arithmetic.  An imported state (init,
+                             set_populations) is held as FP32 pairs until the next step. */
 
 /* ---- element types of caller buffers ---- */
 #define CGEVAP_DTYPE_F64 0
@@ -79,7 +84,7 @@ typedef struct cgevap_params {
   int site_rule;          /* CGEVAP_SITES_GRADIENT, CGEVAP_SITES_BAND or CGEVAP_SITES_GIVEN     */
   double threshold;       /* Gamma (gradient rule) or theta (band rule)                       */
   double sbar;            /* S-bar > 0 of Eq. (relation); varphi = phi / S-bar                */
-  int storage;            /* CGEVAP_F64, CGEVAP_F32, CGEVAP_F16DEV or CGEVAP_BF16DEV          */
+  int storage;            /* CGEVAP_F64, CGEVAP_F32, CGEVAP_F16DEV, CGEVAP_BF16DEV or F32RC   */
 } cgevap_params;
 
 typedef struct cgevap_ledger {

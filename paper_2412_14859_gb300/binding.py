@@ -16,8 +16,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libcgevap.so")
 
-F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
-STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
+F64, F32, F16DEV, BF16DEV, F32RC = 0, 1, 2, 3, 4
+STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV, "f32rc": F32RC}
 DTYPE_F64, DTYPE_F32 = 0, 1
 SITES_GRADIENT, SITES_BAND, SITES_GIVEN = 0, 1, 2
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NAN", -6: "UNSUPPORTED", -7: "IO"}

@@ -93,6 +93,8 @@ cudaError_t launch_volume(const AuxArgs& a, const void* state, double* part, uns
     case 191: CG_VOL(19, ST_F32); break;
     case 192: CG_VOL(19, ST_F16); break;
     case 193: CG_VOL(19, ST_BF16); break;
+    case 94: CG_VOL(9, ST_RC); break;
+    case 194: CG_VOL(19, ST_RC); break;
     default: return cudaErrorInvalidValue;
   }
 #undef CG_VOL

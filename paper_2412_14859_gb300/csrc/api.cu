@@ -48,7 +48,7 @@ std::string validate(const cgevap_params* p) {
   if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND &&
       p->site_rule != CGEVAP_SITES_GIVEN)
     return "unknown site rule";
-  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16DEV) return "unknown storage";
+  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_F32RC) return "unknown storage";
   return "";
 }
 
@@ -105,7 +105,8 @@ AuxArgs cgevap::aux_of(const cgevap_sim* s) {
   a.ph = s->ph;
   mirror_floats(a.ph);
   a.q = s->p.q;
-  a.storage = s->p.storage;
+  // the recolour-on-pull layout holds an imported state as FP32 pairs until the next step
+  a.storage = s->p.storage == CGEVAP_F32RC ? (s->rc_pairs ? ST_F32 : ST_RC) : s->p.storage;
   a.rho_r_in = s->p.rho_r_in;
   a.rho_b_in = s->p.rho_b_in;
   return a;
@@ -113,10 +114,18 @@ AuxArgs cgevap::aux_of(const cgevap_sim* s) {
 
 namespace {
 
+// Arguments of the kernels that write a whole imported state: the recolour-on-pull layout takes
+// it as FP32 pairs (read by the next step's pairs-in kernel).
+AuxArgs import_args(cgevap_sim* s) {
+  if (s->p.storage == CGEVAP_F32RC) s->rc_pairs = 1;
+  return aux_of(s);
+}
+
 KernelRef kernel_for(int q, int storage, int variant) {
   switch (storage) {
     case CGEVAP_F64: return step_kernel_f64(q, variant);
     case CGEVAP_F32: return step_kernel_f32(q, variant);
+    case CGEVAP_F32RC: return step_kernel_rc(q, variant, false);
     default: return step_kernel_dev(q, storage, variant);
   }
 }
@@ -133,6 +142,11 @@ int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
   KernelRef k = family == 1 ? step_tma_f32(s->p.q, variant)
                             : kernel_for(s->p.q, s->p.storage, variant);
   if (!k.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
+  KernelRef k_in{nullptr, 0};
+  if (s->p.storage == CGEVAP_F32RC) {  // same tiles, FP32 pairs in
+    k_in = step_kernel_rc(s->p.q, variant, true);
+    if (!k_in.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
+  }
   TileCfg t = tile_cfg(s->p.q, variant);
   if (k.tx > 0) t = TileCfg{k.tx, k.ty};
   int occ = 0, sms = 0;
@@ -175,6 +189,7 @@ int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
   s->family = family;
   s->variant = variant;
   s->kernel = k;
+  s->kernel_in = k_in;
   s->ntx = ntx;
   s->nty = nty;
   s->pc = best_pc;
@@ -239,9 +254,11 @@ int launch_one_step(cgevap_sim* s) {
     CG_CUDA(s, launch_outlets(aux_of(s), s->state[s->cur], s->outlet_rho[0], s->outlet_rho[1], s->stream));
   StepArgs a = step_args(s);
   void* args[] = {&a, s->tmap[s->cur]};
-  CG_CUDA(s, cudaLaunchKernel(s->kernel.fn, dim3(s->ntx * s->nty, s->nchunk),
-                              dim3(s->kernel.threads), args, s->kernel.smem, s->stream));
+  const KernelRef& k = s->rc_pairs && s->kernel_in.fn ? s->kernel_in : s->kernel;
+  CG_CUDA(s, cudaLaunchKernel(k.fn, dim3(s->ntx * s->nty, s->nchunk), dim3(k.threads), args, k.smem,
+                              s->stream));
   s->cur ^= 1;
+  s->rc_pairs = 0;
   return CGEVAP_OK;
 }
 
@@ -495,6 +512,8 @@ int cgevap_set_flux_heated(cgevap_sim* s, double phi_s, double K, double length,
 
 int cgevap_set_outlets(cgevap_sim* s, double rho_lo, double rho_hi) {
   if (!s) return CGEVAP_ERR_ARG;
+  if (s->p.storage == CGEVAP_F32RC && (rho_lo > 0.0 || rho_hi > 0.0))
+    return fail(s, CGEVAP_ERR_UNSUPPORTED, "outlets need a storage that holds each colour (not F32RC)");
   if (!std::isfinite(rho_lo) || !std::isfinite(rho_hi))
     return fail(s, CGEVAP_ERR_ARG, "outlet densities must be finite");
   const bool lo = rho_lo > 0.0, hi = rho_hi > 0.0;
@@ -525,7 +544,7 @@ int cgevap_init_equilibrium(cgevap_sim* s, const double* dev_rhoN0, const void* 
   if (dev_noise && noise_dtype != CGEVAP_DTYPE_F64 && noise_dtype != CGEVAP_DTYPE_F32)
     return fail(s, CGEVAP_ERR_ARG, "noise dtype must be F64 or F32");
   CG_CUDA(s, cudaSetDevice(s->device));
-  CG_CUDA(s, launch_init_equilibrium(aux_of(s), dev_rhoN0, dev_noise, noise_dtype,
+  CG_CUDA(s, launch_init_equilibrium(import_args(s), dev_rhoN0, dev_noise, noise_dtype,
                                      s->state[s->cur], s->stream));
   CG_CUDA(s, cudaMemsetAsync(s->ledger, 0, sizeof(DevLedger), s->stream));
   s->heat.since = s->heat.every;  // a heated flux field follows the new state
@@ -537,7 +556,7 @@ int cgevap_set_populations(cgevap_sim* s, const void* dev_f, int dtype) {
   if (dtype != CGEVAP_DTYPE_F64 && dtype != CGEVAP_DTYPE_F32)
     return fail(s, CGEVAP_ERR_ARG, "dtype must be F64 or F32");
   CG_CUDA(s, cudaSetDevice(s->device));
-  CG_CUDA(s, launch_set_populations(aux_of(s), dev_f, dtype, s->state[s->cur], s->stream));
+  CG_CUDA(s, launch_set_populations(import_args(s), dev_f, dtype, s->state[s->cur], s->stream));
   s->heat.since = s->heat.every;
   return refresh_gradient_sites(s);
 }
@@ -644,7 +663,7 @@ int cgevap_check_health(cgevap_sim* s) {
 
 // Checkpoint file: magic, version, params, then raw device images (bit-exact restart).
 static const char kMagic[8] = {'C', 'G', 'E', 'V', 'A', 'P', 'C', 'K'};
-static const int kVersion = 1;
+static const int kVersion = 2;  // 2 adds the F32RC layout flag after the ledger
 
 int cgevap_save(cgevap_sim* s, const char* path) {
   if (!s || !path) return CGEVAP_ERR_ARG;
@@ -675,6 +694,7 @@ int cgevap_save(cgevap_sim* s, const char* path) {
             std::fwrite(&has_field, sizeof(int), 1, f) == 1 &&
             std::fwrite(&has_solid, sizeof(int), 1, f) == 1 &&
             std::fwrite(&led, sizeof(led), 1, f) == 1 &&
+            std::fwrite(&s->rc_pairs, sizeof(int), 1, f) == 1 &&
             std::fwrite(state.data(), 1, state.size(), f) == state.size() &&
             std::fwrite(mask.data(), 1, mask.size(), f) == mask.size() &&
             (!has_field || std::fwrite(field.data(), 1, field.size(), f) == field.size()) &&
@@ -690,18 +710,19 @@ int cgevap_load(cgevap_sim* s, const char* path) {
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(s, CGEVAP_ERR_IO, std::string("cannot open ") + path);
   char magic[8];
-  int version = 0, has_field = 0, has_solid = 0;
+  int version = 0, has_field = 0, has_solid = 0, rc_pairs = 1;
   cgevap_params p;
   double phi = 0;
   DevLedger led;
   std::vector<char> state(s->state_bytes), field;
   std::vector<uint8_t> mask(s->N), solid;
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
-            std::fread(&version, sizeof(int), 1, f) == 1 && version == kVersion &&
+            std::fread(&version, sizeof(int), 1, f) == 1 && (version == 1 || version == kVersion) &&
             std::fread(&p, sizeof(p), 1, f) == 1 && std::fread(&phi, sizeof(double), 1, f) == 1 &&
             std::fread(&has_field, sizeof(int), 1, f) == 1 &&
             std::fread(&has_solid, sizeof(int), 1, f) == 1 &&
-            std::fread(&led, sizeof(led), 1, f) == 1;
+            std::fread(&led, sizeof(led), 1, f) == 1 &&
+            (version == 1 || std::fread(&rc_pairs, sizeof(int), 1, f) == 1);
   if (ok && std::memcmp(&p, &s->p, sizeof(p)) != 0) {
     std::fclose(f);
     return fail(s, CGEVAP_ERR_ARG, "checkpoint parameters differ from the handle's");
@@ -744,6 +765,7 @@ int cgevap_load(cgevap_sim* s, const char* path) {
   CG_CUDA(s, cudaMemcpyAsync(s->state[s->cur], state.data(), s->state_bytes, cudaMemcpyHostToDevice, s->stream));
   CG_CUDA(s, cudaMemcpyAsync(s->mask[s->cur], mask.data(), s->N, cudaMemcpyHostToDevice, s->stream));
   CG_CUDA(s, cudaMemcpyAsync(s->ledger, &led, sizeof(led), cudaMemcpyHostToDevice, s->stream));
+  s->rc_pairs = rc_pairs;
   CG_CUDA(s, cudaStreamSynchronize(s->stream));
   return CGEVAP_OK;
 }
@@ -779,6 +801,7 @@ double cgevap_bytes_per_update(const cgevap_sim* s) {
   switch (s->p.storage) {
     case CGEVAP_F64: pops = 2.0 * 2 * Q * 8; break;
     case CGEVAP_F32: pops = 2.0 * 2 * Q * 4; break;
+    case CGEVAP_F32RC: pops = 2.0 * (Q * 4 + 16); break;
     default: pops = 2.0 * (8 + (Q - 1) * 4); break;
   }
   const double mask = s->p.site_rule == CGEVAP_SITES_BAND ? 1.0 : 2.0;  // read + write

@@ -260,7 +260,14 @@ __global__ void k_fill_ghosts(Geom g, void* state) {
     const Coord c = coord_of(g, cell);
     const Images im = images_of(g, c.a, c.b, c.m);
     if (im.n < 2) continue;
-    if (Storage<S>::dev) {
+    if constexpr (Storage<S>::rc) {
+      float* pop = reinterpret_cast<float*>(state);
+      float4* rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(state) + rc_record_offset(Q, g.nstore));
+      for (int j = 1; j < im.n; ++j) {
+        rec[im.s[j]] = rec[im.s[0]];
+        for (int i = 0; i < Q; ++i) pop[(size_t)i * g.nstore + im.s[j]] = pop[(size_t)i * g.nstore + im.s[0]];
+      }
+    } else if (Storage<S>::dev) {
       float2* rest = reinterpret_cast<float2*>(state);
       uint32_t* dev = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(state) + dev_block_offset(g.nstore));
       for (int j = 1; j < im.n; ++j) {
@@ -332,7 +339,9 @@ __global__ void k_convert(const void* in, int in_dt, void* out, int out_double, 
 template <int S>
 __device__ __forceinline__ void store_blue(void* state, const Geom& g, const Physics& ph, int dir,
                                            int si, double v) {
-  if constexpr (Storage<S>::dev) {
+  if constexpr (Storage<S>::rc) {
+    return;  // not launched for this layout (launch_outlets refuses it)
+  } else if constexpr (Storage<S>::dev) {
     using P = typename Storage<S>::packed;
     const float f0b = reinterpret_cast<const float2*>(state)[si].y;
     P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(state) + dev_block_offset(g.nstore)) +
@@ -428,6 +437,8 @@ __global__ void k_fill(double* out, double v, long long n) {
       case 191: KERNEL<19, ST_F32><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
       case 192: KERNEL<19, ST_F16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
       case 193: KERNEL<19, ST_BF16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;           \
+      case 94: KERNEL<9, ST_RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;               \
+      case 194: KERNEL<19, ST_RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;             \
       default: return cudaErrorInvalidValue;                                                      \
     }                                                                                             \
   } while (0)
@@ -519,6 +530,7 @@ cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int ou
 }
 
 cudaError_t launch_outlets(const AuxArgs& a, void* state, double rho_lo, double rho_hi, cudaStream_t s) {
+  if (a.storage == ST_RC) return cudaErrorInvalidValue;  // a colour-blind layout holds no blue half
   CGEVAP_DISPATCH(a, k_outlet, grid_for(2LL * a.g.na * a.g.nb), s, a.g, a.ph, state, rho_lo, rho_hi);
   return cudaGetLastError();
 }

@@ -148,6 +148,76 @@ struct PopIO<S, Q, false> {
   }
 };
 
+// Recolour-on-pull layout: either colour of a direction from the colour-blind population and the
+// cell's record (w_r, V); `dir` is the stored direction (opp(i) for a bounced-back link, whose
+// c . V is the negative of direction i's).
+template <int Q>
+struct RcIO {
+  using L = Lattice<Q>;
+  static __device__ __forceinline__ const float4* rec(const void* base, int nstore) {
+    return reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) +
+                                           rc_record_offset(Q, nstore));
+  }
+  static __device__ __forceinline__ V2<float> load(const void* base, int nstore, int i, int dir,
+                                                   int si) {
+    const float f = __ldg(reinterpret_cast<const float*>(base) + (size_t)dir * nstore + si);
+    if (i == 0) {
+      const float wr = __ldg(reinterpret_cast<const float*>(rec(base, nstore) + si));
+      const float fr = wr * f;
+      return {fr, f - fr};
+    }
+    const float4 r = __ldg(rec(base, nstore) + si);
+    float cv = 0.0f;
+    if (L::ca(i) > 0) cv += r.y;
+    if (L::ca(i) < 0) cv -= r.y;
+    if (L::cb(i) > 0) cv += r.z;
+    if (L::cb(i) < 0) cv -= r.z;
+    if (L::cm(i) > 0) cv += r.w;
+    if (L::cm(i) < 0) cv -= r.w;
+    if (dir != i) cv = -cv;
+    const float fr = fmaf(r.x, f, float(rc_factor<L>(i)) * cv);
+    return {fr, f - fr};
+  }
+  // Writes f = r + b for direction i; with i = 0 also the record (w_r = r / (r + b), V = 0).
+  // Exact for the states this layout can hold with V = 0 (used to zero solid cells).
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, float r, float b) {
+    const float f = r + b;
+    reinterpret_cast<float*>(base)[(size_t)i * nstore + si] = f;
+    if (i == 0) {
+      float4* rc = reinterpret_cast<float4*>(reinterpret_cast<char*>(base) + rc_record_offset(Q, nstore));
+      rc[si] = make_float4(f > 0.0f ? r / f : 0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+};
+
+template <int Q>
+struct PopIO<ST_RC, Q, false> {
+  using R = float;
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int i, int dir, int si,
+                                               const Physics&) {
+    return RcIO<Q>::load(base, nstore, i, dir, si);
+  }
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
+                                               V2<R>, const Physics&) {
+    RcIO<Q>::store(base, nstore, i, si, r, b);
+  }
+};
+
+// Pairs in (an imported state), recolour-on-pull out.
+template <int Q>
+struct PopIO<ST_RCI, Q, false> {
+  using R = float;
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int, int dir, int si,
+                                               const Physics&) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(base) + (size_t)dir * nstore + si);
+    return {v.x, v.y};
+  }
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
+                                               V2<R>, const Physics&) {
+    RcIO<Q>::store(base, nstore, i, si, r, b);
+  }
+};
+
 template <int S, int Q>
 struct PopIO<S, Q, true> {
   using R = float;

@@ -118,7 +118,16 @@ __host__ __device__ constexpr uint32_t dirs_where(int axis, int sign) {
 //   kappa_i^k = phi_i(alpha_k) / phi_0(alpha_k) is the ratio of the rest state of component k,
 //   so bulk cells at rest store deviations near 0; s is a power of two (FP16 only) that keeps
 //   small deviations out of the subnormal range.  Decoding multiplies by 1/s exactly.
-enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+// ST_RC ("recolour on pull"): float pops[i][cell] = the colour-blind post-collision population
+//   f_i, and one float4 rec[cell] = (w_r, V) after the Q planes, from which either colour of any
+//   direction follows exactly as Eq. (recolor) forms it:
+//     f_i^r = w_r f_i + s_|c_i| (c_i . V),   f_i^b = f_i - f_i^r,
+//   w_r = rho_r / rho, V = beta (rho_r rho_b / rho) (1 - abar) F / |F| and s = A_s / |c| for the
+//   speed class s (phi_i(abar) = A_s (1 - abar) for i >= 1), 0 for the rest direction.  Q + 4
+//   floats per cell instead of 2Q.  Arbitrary population pairs (an initial state with noise,
+//   an import) are not of this form: those are held as FP32 pairs and the first step reads them
+//   with ST_RCI (pairs in, ST_RC out).
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_RC = 4, ST_RCI = 5 };
 
 template <int S>
 struct Storage;
@@ -127,6 +136,7 @@ struct Storage<ST_F64> {
   using real = double;
   using vec = double2;
   static constexpr bool dev = false;
+  static constexpr bool rc = false;
   static constexpr int bytes_per_pop = 8;
 };
 template <>
@@ -134,6 +144,23 @@ struct Storage<ST_F32> {
   using real = float;
   using vec = float2;
   static constexpr bool dev = false;
+  static constexpr bool rc = false;
+  static constexpr int bytes_per_pop = 4;
+};
+template <>
+struct Storage<ST_RC> {  // reads and writes the recolour-on-pull layout
+  using real = float;
+  using vec = float2;
+  static constexpr bool dev = false;
+  static constexpr bool rc = true;
+  static constexpr int bytes_per_pop = 4;
+};
+template <>
+struct Storage<ST_RCI> {  // reads FP32 pairs, writes the recolour-on-pull layout
+  using real = float;
+  using vec = float2;
+  static constexpr bool dev = false;
+  static constexpr bool rc = true;
   static constexpr int bytes_per_pop = 4;
 };
 template <>
@@ -141,6 +168,7 @@ struct Storage<ST_F16> {
   using real = float;
   using packed = __half2;
   static constexpr bool dev = true;
+  static constexpr bool rc = false;
   static constexpr int bytes_per_pop = 2;
   static __device__ __forceinline__ float2 unpack(packed p) { return __half22float2(p); }
   static __device__ __forceinline__ packed pack(float r, float b) { return __floats2half2_rn(r, b); }
@@ -150,6 +178,7 @@ struct Storage<ST_BF16> {
   using real = float;
   using packed = __nv_bfloat162;
   static constexpr bool dev = true;
+  static constexpr bool rc = false;
   static constexpr int bytes_per_pop = 2;
   static __device__ __forceinline__ float2 unpack(packed p) { return __bfloat1622float2(p); }
   static __device__ __forceinline__ packed pack(float r, float b) {
@@ -179,10 +208,23 @@ __host__ inline StoreShape store_shape(int q, int nx, int ny, int nz) {
   return s;
 }
 
+// Byte offset of the recolouring records inside an ST_RC state buffer.
+__host__ __device__ inline size_t rc_record_offset(int q, long long nstore) {
+  return (size_t)q * nstore * sizeof(float);
+}
+
+// Recolouring factor s_|c| = A_s / |c| of ST_RC for direction i (0 for the rest direction).
+template <class L>
+__host__ __device__ constexpr double rc_factor(int i) {
+  return L::speed2(i) == 0 ? 0.0 : L::A(i) * inv_norm<L>(i);
+}
+
 __host__ inline size_t state_bytes(int storage, int q, long long nstore) {
   switch (storage) {
     case ST_F64: return (size_t)q * nstore * sizeof(double2);
-    case ST_F32: return (size_t)q * nstore * sizeof(float2);
+    case ST_F32:
+    case ST_RC:  // room for the FP32 pairs of an imported state
+    case ST_RCI: return (size_t)q * nstore * sizeof(float2);
     default: return dev_block_offset(nstore) + (size_t)(q - 1) * nstore * 4;
   }
 }

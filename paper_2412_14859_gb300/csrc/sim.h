@@ -42,6 +42,8 @@ struct cgevap_sim {
   int family = 0;  // 0 register-pipelined kernel, 1 TMA-pipelined kernel
   int variant = 0;
   cgevap::KernelRef kernel{nullptr, 0};
+  cgevap::KernelRef kernel_in{nullptr, 0};  // F32RC: the same step reading FP32 pairs
+  int rc_pairs = 1;  // F32RC: state[cur] holds FP32 pairs (created or imported, not yet stepped)
   alignas(64) unsigned char tmap[2][128];  // TMA tensor maps of state[0] and state[1]
   int ntx = 1, nty = 1, pc = 1, nchunk = 1;
   cgevap::AdjointTape* tape = nullptr;  // checkpoints of cgevap_adjoint_forward (adjoint.cu)

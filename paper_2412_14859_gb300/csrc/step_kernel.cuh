@@ -264,6 +264,56 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
   }
 }
 
+// Recolour-on-pull layout: pull one cell's colour-blind populations and split each into its
+// colours with the source cell's record (w_r, V), staged in shared memory; recbox(q, y, x) as
+// restbox above.  f_i^r = w_r f_i + s_|c| (c_dir . V) with dir the stored direction (opp(i),
+// c_dir = -c_i, for a bounced link, whose source is the cell itself).  Of the pulled pairs the
+// step uses only the colour-blind sums g_i^r + g_i^b and the two colour totals (Eq. exchange
+// moves mass between the rest pair alone), so the red of every direction is gathered into the
+// rest pair: g_0 = (sum_i f_i^r, f_0 - sum_i f_i^r), g_i = (0, f_i) for i >= 1.  That holds Q + 1
+// values instead of 2Q.
+template <int Q, class RecBox>
+__device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, int si,
+                                             PlaneOffsets po, uint32_t sbits, int ex, int ey,
+                                             const int (&ps)[3], const RecBox& recbox,
+                                             V2<float> (&g)[Q]) {
+  using L = Lattice<Q>;
+  const float* pop = reinterpret_cast<const float*>(A.pin);
+  float fv[Q];
+  // all population loads first
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+    int dir = i;
+    if (sbits) {
+      const bool bounce = (sbits >> i) & 1u;
+      src = bounce ? si : src;
+      dir = bounce ? opp(i) : i;
+    }
+    fv[i] = __ldg(pop + (size_t)dir * A.g.nstore + src);
+  }
+  const float4 r0 = recbox(ps[1], ey, ex);
+  float red = r0.x * fv[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const bool bounce = sbits && ((sbits >> i) & 1u);
+    const float4 r = bounce ? r0 : recbox(ps[1 + L::cm(i)], ey - L::cb(i), ex - L::ca(i));
+    float cv = 0.0f;
+    if (L::ca(i) > 0) cv += r.y;
+    if (L::ca(i) < 0) cv -= r.y;
+    if (L::cb(i) > 0) cv += r.z;
+    if (L::cb(i) < 0) cv -= r.z;
+    if (L::cm(i) > 0) cv += r.w;
+    if (L::cm(i) < 0) cv -= r.w;
+    if (bounce) cv = -cv;
+    red += fmaf(r.x, fv[i], float(rc_factor<L>(i)) * cv);
+    g[i] = {0.0f, fv[i]};
+  }
+  g[0] = {red, fv[0] - red};
+}
+
 template <class R>
 __device__ __forceinline__ void norm_pair(R F2, R& Fn, R& iFn);
 template <>
@@ -347,9 +397,27 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   const R f0eq = fma(rwc[0], -uu15, restc[0]);
   const R fi0 = fma(itau, f0eq - f[0], f[0]) - kc[0];
   const V2<R> f0{wr * fi0, fi0 - wr * fi0};
-  IO::store(A.pout, A.g.nstore, 0, si, f0.r, f0.b, f0, ph);
-  if (GHOSTS && nimg)
-    for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0.r, f0.b, f0, ph);
+  float* const rc_pop = reinterpret_cast<float*>(A.pout);  // recolour-on-pull layout only
+  (void)rc_pop;
+  if constexpr (Storage<S>::rc) {
+    // colour-blind populations plus the record (w_r, V) from which the reader recolours:
+    // kr_s (F.c_i) = s_|c| (c_i . V) with V = beta (rho_r rho_b / rho) (1 - abar) F / |F|
+    const R gv = rcol * iFn * rho * (R(1) - abar);
+    const float4 rec = make_float4(wr, gv * Fa, gv * Fb, gv * Fm);
+    float4* const rc_rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(A.pout) +
+                                                     rc_record_offset(Q, A.g.nstore));
+    rc_pop[si] = fi0;
+    rc_rec[si] = rec;
+    if (GHOSTS && nimg)
+      for (int j = 0; j < nimg; ++j) {
+        rc_pop[si + dimg[j]] = fi0;
+        rc_rec[si + dimg[j]] = rec;
+      }
+  } else {
+    IO::store(A.pout, A.g.nstore, 0, si, f0.r, f0.b, f0, ph);
+    if (GHOSTS && nimg)
+      for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0.r, f0.b, f0, ph);
+  }
   static_assert(opposites_adjacent<L>(), "directions (i, i+1), i odd, must be opposite");
   // Opposite directions (i, i+1) share |c.u|, |c.F| with opposite signs: the even part of Eq.
   // (feq) and the perturbation are common, the odd part of Eq. (feq) and the recoloring term
@@ -388,12 +456,23 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
       fri = fma(wr, fi, kp);
       frj = fma(wr, fj, -kp);
     }
-    IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
-    IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
-    if (GHOSTS && nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
-      for (int k = 0; k < nimg; ++k) {
-        IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
-        IO::store(A.pout, A.g.nstore, j, si + dimg[k], frj, fj - frj, f0, ph);
+    if constexpr (Storage<S>::rc) {
+      const size_t ns = (size_t)A.g.nstore;
+      rc_pop[i * ns + si] = fi;
+      rc_pop[j * ns + si] = fj;
+      if (GHOSTS && nimg)
+        for (int k = 0; k < nimg; ++k) {
+          rc_pop[i * ns + si + dimg[k]] = fi;
+          rc_pop[j * ns + si + dimg[k]] = fj;
+        }
+    } else {
+      IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
+      IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
+      if (GHOSTS && nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
+        for (int k = 0; k < nimg; ++k) {
+          IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
+          IO::store(A.pout, A.g.nstore, j, si + dimg[k], frj, fj - frj, f0, ph);
+        }
       }
     }
   }
@@ -462,10 +541,13 @@ struct TileSmem {
   static constexpr int TH = TY * CPT;
   static constexpr int HX = TX + 2, HY = L::D3 ? TH + 2 : 1;
   static constexpr bool DEV = Storage<S>::dev;
-  static constexpr int RX = DEV ? TX + 4 : 1, RY = DEV ? (L::D3 ? TH + 4 : 1) : 1, RS = DEV ? 3 : 1;
+  // source staging: rest pairs (deviation storages) or recolouring records (ST_RC)
+  static constexpr bool STAGE = DEV || S == ST_RC;
+  static constexpr int BOX = S == ST_RC ? 16 : 8;
+  static constexpr int RX = STAGE ? TX + 4 : 1, RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1, RS = STAGE ? 3 : 1;
   // every part starts on a 16-byte boundary
   static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
-  static constexpr int REST = ((RS * RY * RX * 8) + 15) & ~15;
+  static constexpr int REST = ((RS * RY * RX * BOX) + 15) & ~15;
   static constexpr int PARK = ((CPT * Q * TX * TY * (int)sizeof(R)) + 15) & ~15;
   static constexpr int BYTES = RING + REST + PARK;
   static_assert(RING % 16 == 0 && REST % 16 == 0 && BYTES % 16 == 0, "16-byte aligned parts");
@@ -502,9 +584,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   R(*ring)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ring_mem);
   // deviation storage: rest pairs of the tile plus a two-cell ring, planes m .. m+2
   constexpr bool DEV = Storage<S>::dev;
-  constexpr int RX = DEV ? TX + 4 : 1;
-  constexpr int RY = DEV ? (L::D3 ? TH + 4 : 1) : 1;
-  constexpr int RS = DEV ? 3 : 1;
+  constexpr bool RCIN = S == ST_RC;      // reads the recolour-on-pull layout
+  constexpr bool STAGE = DEV || RCIN;    // pulls read per-source data staged in shared memory
+  constexpr int RX = STAGE ? TX + 4 : 1;
+  constexpr int RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1;
+  constexpr int RS = STAGE ? 3 : 1;
   constexpr int RN = RX * RY;
   constexpr int RPT = (RN + NT - 1) / NT;  // rest-box elements staged per thread
   float2(*rest_ring)[RY][RX] = reinterpret_cast<float2(*)[RY][RX]>(rest_mem);
@@ -559,7 +643,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   for (int k = 0; k < RPT; ++k) {
     rest_off[k] = -1;
     const int e = tid + k * NT;
-    if (DEV && e < RN) {
+    if (STAGE && e < RN) {
       const int ex = e % RX, ey = e / RX;
       int a = a0 - 2 + ex, b = L::D3 ? b0 - 2 + ey : 0;
       bool ok = true;
@@ -574,19 +658,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   }
   const int plane_stride = G.rows * G.pitch;
   auto rest_slot = [&](int uq) { return (uq - m0 + 3) % 3; };
-  auto stage_rest = [&](int uq) {  // rest pairs of plane uq (unwrapped) into its slot
-    if (!DEV) return;
+  // ST_RC: the recolouring records (w_r, V) of the same box, staged the same way
+  float4(*rec_ring)[RY][RX] = reinterpret_cast<float4(*)[RY][RX]>(rest_mem);
+  auto stage_rest = [&](int uq) {  // rest pairs / records of plane uq (unwrapped) into its slot
+    if (!STAGE) return;
     const Plane q = make_plane(G, uq);
-    const float2* rest = reinterpret_cast<const float2*>(A.pin);
     const int sl = rest_slot(uq);
+    if constexpr (RCIN) {
+      const float4* rec = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(A.pin) +
+                                                          rc_record_offset(Q, G.nstore));
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      const int e = tid + k * NT;
-      if (e < RN && q.ok && rest_off[k] >= 0)
-        rest_ring[sl][e / RX][e % RX] = __ldg(rest + q.m * plane_stride + rest_off[k]);
+      for (int k = 0; k < RPT; ++k) {
+        const int e = tid + k * NT;
+        if (e < RN && q.ok && rest_off[k] >= 0)
+          rec_ring[sl][e / RX][e % RX] = __ldg(rec + q.m * plane_stride + rest_off[k]);
+      }
+    } else {
+      const float2* rest = reinterpret_cast<const float2*>(A.pin);
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int e = tid + k * NT;
+        if (e < RN && q.ok && rest_off[k] >= 0)
+          rest_ring[sl][e / RX][e % RX] = __ldg(rest + q.m * plane_stride + rest_off[k]);
+      }
     }
   };
   auto restbox = [&](int slot, int y, int x) -> float2 { return rest_ring[slot][y][x]; };
+  auto recbox = [&](int slot, int y, int x) -> float4 { return rec_ring[slot][y][x]; };
 
   // The colour-blind sums of the next plane's pulled, post-exchange populations wait in
   // thread-private columns of shared memory (only this thread reads or writes its columns, so no
@@ -613,7 +711,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
     const PlaneOffsets po = plane_offsets(G, p.m);
     const int slot = (um - m0 + 1) & 3;
     int ps[3] = {0, 0, 0};
-    if (DEV) {  // the pulls of plane um read the rest pairs of planes um-1 .. um+1
+    if (STAGE) {  // the pulls of plane um read the staged data of planes um-1 .. um+1
       stage_rest(um + 1);
       __syncthreads();
       ps[0] = rest_slot(um + 1);
@@ -631,6 +729,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         if constexpr (DEV)
           pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                               L::D3 ? hy + 1 : 0, ps, restbox, tmp);
+        else if constexpr (RCIN)
+          pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1, L::D3 ? hy + 1 : 0,
+                          ps, recbox, tmp);
         else
           pull_cell<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, tmp);
         rn = site_exchange<Q, S>(A, cell, tmp, t_rr, t_rb, t_e, t_flags, t_irho);
@@ -648,6 +749,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         if constexpr (DEV)
           pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                               L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c]);
+        else if constexpr (RCIN)
+          pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
+                          L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c]);
         else
           pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
       }
@@ -678,7 +782,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
       for (int i = 0; i < Q; ++i) parked[(c * Q + i) * NT + tid] = g[c][i].r + g[c][i].b;
   }
-  if (DEV) __syncthreads();  // the first fill below restages a rest slot the pulls above read
+  if (STAGE) __syncthreads();  // the first fill below restages a slot the pulls above read
 
   const int m_end = iters < 0 ? m1 : m0 + iters;
   for (int m = m0; m < m_end; ++m) {

@@ -1,0 +1,49 @@
+// step_rc.cu -- instantiations of the fused step for the recolour-on-pull layout (ST_RC): FP32
+// arithmetic, Q colour-blind populations plus one (w_r, V) record per cell.  ST_RCI is the same
+// step reading an imported state held as FP32 pairs.
+#include "launch.h"
+#include "step_kernel.cuh"
+
+namespace cgevap {
+
+template <int Q, int S, int TX, int TY, int MINB, int CPT>
+static KernelRef rc_ref() {
+  constexpr int smem = TileSmem<Q, S, TX, TY, CPT>::BYTES;
+  const void* fn = (const void*)cg_step_kernel<Q, S, TX, TY, MINB, CPT>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return {nullptr, 0};
+    attr = true;
+  }
+  KernelRef k{fn, TX * TY};
+  k.smem = smem;
+  k.tx = TX;
+  k.ty = TY * CPT;
+  return k;
+}
+
+template <int S>
+static KernelRef pick(int q, int variant) {
+  if (q == 19) {
+    switch (variant) {
+      case 0: return rc_ref<19, S, 32, 4, 4, 1>();
+      case 1: return rc_ref<19, S, 16, 8, 4, 1>();
+      case 2: return rc_ref<19, S, 32, 4, 3, 1>();  // 168 registers, three CTAs per SM
+      case 3: return rc_ref<19, S, 16, 4, 8, 1>();
+      case 4: return rc_ref<19, S, 16, 8, 3, 1>();
+    }
+  } else if (q == 9) {
+    switch (variant) {
+      case 0: return rc_ref<9, S, 128, 1, 4, 1>();
+      case 1: return rc_ref<9, S, 64, 1, 8, 1>();
+    }
+  }
+  return {nullptr, 0};
+}
+
+KernelRef step_kernel_rc(int q, int variant, bool pairs_in) {
+  return pairs_in ? pick<ST_RCI>(q, variant) : pick<ST_RC>(q, variant);
+}
+
+}  // namespace cgevap

@@ -9,6 +9,7 @@ from dataclasses import replace
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2412_14859_gb300 import inputs
@@ -17,8 +18,8 @@ from harness import gpu_sim, oracle_run, rel_linf
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f32:reg": 1e-5, "f32:tma": 1e-5}
-STORAGES = ["f64", "f32:reg", "f32:tma"]
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32:reg": 1e-5, "f32:tma": 1e-5, "f32rc": 1e-5}
+STORAGES = ["f64", "f32:reg", "f32:tma", "f32rc"]
 
 
 def drop(q, shape, **kw):
@@ -135,7 +136,7 @@ def test_gradient_rule_initial_sites_fp64():
     assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, run.mask[far])
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f32rc"])
 @pytest.mark.parametrize("q,nvar", [(19, 5), (9, 2)])
 def test_every_kernel_variant_matches_oracle(storage, q, nvar):
     """Each tile shape / occupancy variant of the register-pipelined step computes the same
@@ -174,13 +175,14 @@ def test_flat_slab_workload_full_run():
     assert led["evaporated"] == pytest.approx(run.evaporated, rel=1e-12)
 
 
-def test_flat_slab_fp32_drift_over_full_run():
+@pytest.mark.parametrize("storage", ["f32", "f32rc"])
+def test_flat_slab_fp32_drift_over_full_run(storage):
     """The same 2000 steps in FP32: rounding accumulates at the interface (relative L-inf of rho_r
     grows to ~1e-4; the 1e-5 parity bound holds over the tens of steps of the tests above), the
     red mass stays within 1e-5 (measured 2.8e-6) and the sites are those of the oracle."""
     case = inputs.flat_slab_2d()
     run = oracle_run(case, case.steps)
-    sim = gpu_sim(case, "f32")
+    sim = gpu_sim(case, storage)
     sim.step(case.steps)
     g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
     o = run.macros()
@@ -188,3 +190,26 @@ def test_flat_slab_fp32_drift_over_full_run():
     assert abs(g["rho_r"].sum() - o["rho_r"].sum()) <= 1e-5 * o["rho_r"].sum()
     assert np.array_equal(sim.mask().cpu().numpy() & 1, run.mask)
     assert sim.ledger()["site_steps"] == run.ledger.site_steps
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_recolour_on_pull_restarts_bit_exactly(q, tmp_path):
+    """F32RC holds the colour-blind populations and a per-cell recolouring record; a checkpoint
+    taken right after the import (FP32 pairs) and one taken after steps (the compact layout) both
+    restart bit for bit, and the layout gives the pair storage's result within FP32 rounding."""
+    shape = (12, 21, 37) if q == 19 else (1, 37, 131)
+    case = drop(q, shape, R0=5.0, phi=1e-5)
+    for warm in (0, 7):
+        sim = gpu_sim(case, "f32rc")
+        sim.step(warm)
+        path = str(tmp_path / f"rc{warm}.ckpt")
+        sim.save(path)
+        sim.step(9)
+        a = sim.populations(torch.float32).cpu().numpy()
+        other = gpu_sim(case, "f32rc")
+        other.load(path)
+        other.step(9)
+        assert np.array_equal(other.populations(torch.float32).cpu().numpy(), a)
+    pairs = gpu_sim(case, "f32")
+    pairs.step(16)
+    assert rel_linf(a, pairs.populations(torch.float32).cpu().numpy()) <= 1e-5

@@ -19,13 +19,14 @@ from paper_2412_14859_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
-HEADER = 8 + 4 + 112 + 8 + 4 + 4 + 40  # checkpoint: magic, version, params, phi, flags, ledger
+# checkpoint: magic, version, params, phi, flags, ledger, layout flag
+HEADER = 8 + 4 + 112 + 8 + 4 + 4 + 40 + 4
 
 
 def read_checkpoint(sim, path, ncell):
     sim.save(path)
     raw = open(path, "rb").read()
-    ledger = raw[HEADER - 40:HEADER]
+    ledger = raw[HEADER - 44:HEADER - 4]
     state = raw[HEADER:len(raw) - ncell]
     mask = raw[len(raw) - ncell:]
     return state, mask, ledger
