@@ -267,11 +267,9 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
 // Recolour-on-pull layout: pull one cell's colour-blind populations and split each into its
 // colours with the source cell's record (w_r, V), staged in shared memory; recbox(q, y, x) as
 // restbox above.  f_i^r = w_r f_i + s_|c| (c_dir . V) with dir the stored direction (opp(i),
-// c_dir = -c_i, for a bounced link, whose source is the cell itself).  Of the pulled pairs the
-// step uses only the colour-blind sums g_i^r + g_i^b and the two colour totals (Eq. exchange
-// moves mass between the rest pair alone), so the red of every direction is gathered into the
-// rest pair: g_0 = (sum_i f_i^r, f_0 - sum_i f_i^r), g_i = (0, f_i) for i >= 1.  That holds Q + 1
-// values instead of 2Q.
+// c_dir = -c_i, for a bounced link, whose source is the cell itself).  Each direction keeps its
+// own blue part f_i - f_i^r: the blue total is then a sum of small terms, not the difference of
+// two large ones (which would cost the density-ratio-10 case its FP32 tolerance).
 template <int Q, class RecBox>
 __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, int si,
                                              PlaneOffsets po, uint32_t sbits, int ex, int ey,
@@ -295,7 +293,10 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
     fv[i] = __ldg(pop + (size_t)dir * A.g.nstore + src);
   }
   const float4 r0 = recbox(ps[1], ey, ex);
-  float red = r0.x * fv[0];
+  {
+    const float fr = r0.x * fv[0];
+    g[0] = {fr, fv[0] - fr};
+  }
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const bool bounce = sbits && ((sbits >> i) & 1u);
@@ -308,10 +309,9 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
     if (L::cm(i) > 0) cv += r.w;
     if (L::cm(i) < 0) cv -= r.w;
     if (bounce) cv = -cv;
-    red += fmaf(r.x, fv[i], float(rc_factor<L>(i)) * cv);
-    g[i] = {0.0f, fv[i]};
+    const float fr = fmaf(r.x, fv[i], float(rc_factor<L>(i)) * cv);
+    g[i] = {fr, fv[i] - fr};
   }
-  g[0] = {red, fv[0] - red};
 }
 
 template <class R>
