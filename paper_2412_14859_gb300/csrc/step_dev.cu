@@ -44,11 +44,11 @@ template <int S>
 static KernelRef pick(int q, int variant) {
   if (q == 19) {
     switch (variant) {
-      case 0: return reg_ref<19, S, 32, 4, 4, 1>();
+      case 0: return reg_ref<19, S, 16, 8, 4, 1>();  // the fastest: smallest staged box per cell
       case 1: return dev_ref<19, S, 32, 8, 2, 1>();
       case 2: return reg_ref<19, S, 16, 16, 2, 1>();
       case 3: return dev_ref<19, S, 32, 4, 4, 1>();
-      case 4: return reg_ref<19, S, 16, 8, 4, 1>();
+      case 4: return reg_ref<19, S, 32, 4, 4, 1>();
     }
   } else if (q == 9) {
     switch (variant) {

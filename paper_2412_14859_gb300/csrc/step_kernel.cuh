@@ -130,6 +130,35 @@ __device__ __forceinline__ float recip<float>(float x) {
 // Steps 2-4 for one cell whose pulled populations are in g: decide whether it is a site, apply
 // Eq. (exchange).  Returns rho^N after the exchange; g, rr, rb become post-exchange and irho is
 // 1 / rho (rho is not changed by the exchange).
+// The decision and Eq. (exchange) from the colour totals sr, sb of the pulled populations:
+// returns rho^N after the exchange and sets rr, rb (post-exchange), e (mass moved), flags, irho.
+template <int S>
+__device__ __forceinline__ typename Storage<S>::real exchange_from_sums(
+    const StepArgs& A, int cell, typename Storage<S>::real sr, typename Storage<S>::real sb,
+    typename Storage<S>::real& rr, typename Storage<S>::real& rb, typename Storage<S>::real& e,
+    uint32_t& flags, typename Storage<S>::real& irho) {
+  using R = typename Storage<S>::real;
+  irho = recip<R>(sr + sb);
+  const R rn_pre = (sr - sb) * irho;
+  bool site, near;
+  if (A.ph.rule == 1) {
+    const R d = fabs(rn_pre) - PHYS(R, A.ph, threshold);
+    site = d < R(0);
+    near = fabs(d) < R(1e-6);
+  } else {
+    // gradient rule: the decision of the previous step (bit 1); given rule: bit 0
+    const uint32_t mb = A.mask_in[cell];
+    const int sh = A.ph.rule == 2 ? 0 : 1;
+    site = (mb >> sh) & 1u;
+    near = (mb >> (sh + 2)) & 1u;
+  }
+  e = site ? flux_at<S>(A.ph, cell) : R(0);
+  rr = sr - e;
+  rb = sb + e;
+  flags = (site ? 1u : 0u) | (near ? 4u : 0u);
+  return rn_pre - R(2) * e * irho;
+}
+
 template <int Q, int S>
 __device__ __forceinline__ typename Storage<S>::real site_exchange(
     const StepArgs& A, int cell, V2<typename Storage<S>::real> (&g)[Q],
@@ -150,27 +179,10 @@ __device__ __forceinline__ typename Storage<S>::real site_exchange(
       sb += g[i].b;
     }
   }
-  irho = recip<R>(sr + sb);
-  const R rn_pre = (sr - sb) * irho;
-  bool site, near;
-  if (A.ph.rule == 1) {
-    const R d = fabs(rn_pre) - PHYS(R, A.ph, threshold);
-    site = d < R(0);
-    near = fabs(d) < R(1e-6);
-  } else {
-    // gradient rule: the decision of the previous step (bit 1); given rule: bit 0
-    const uint32_t mb = A.mask_in[cell];
-    const int sh = A.ph.rule == 2 ? 0 : 1;
-    site = (mb >> sh) & 1u;
-    near = (mb >> (sh + 2)) & 1u;
-  }
-  e = site ? flux_at<S>(A.ph, cell) : R(0);
+  const R rn = exchange_from_sums<S>(A, cell, sr, sb, rr, rb, e, flags, irho);
   g[0].r -= e;
   g[0].b += e;
-  rr = sr - e;
-  rb = sb + e;
-  flags = (site ? 1u : 0u) | (near ? 4u : 0u);
-  return rn_pre - R(2) * e * irho;
+  return rn;
 }
 
 // Storage offsets from a cell in plane m to its pull sources in planes m-1 (dm_lo, used by
@@ -221,12 +233,15 @@ __device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int
 // Deviation storage: pull one cell whose source rest populations are staged in shared memory.
 // restbox(q, y, x) is the (f_0^r, f_0^b) pair of the cell at box row y, column x of plane slot q;
 // (ex, ey) is this cell's own box position and ps[k] the slot of plane m + 1 - k, so the source
-// plane m - c_m of direction i is ps[1 + c_m].
+// plane m - c_m of direction i is ps[1 + c_m].  The step needs of the pulled pairs only the
+// colour-blind values and the two colour totals (Eq. exchange changes the totals, not the
+// colour-blind rest population), so that is what comes out: g_i = (f_i^r + f_i^b, 0) and
+// (sr, sb) = the sums of each colour over i; Q + 2 live values instead of 2Q.
 template <int Q, int S, class RestBox>
 __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl, int si,
                                               PlaneOffsets po, uint32_t sbits, int ex, int ey,
                                               const int (&ps)[3], const RestBox& restbox,
-                                              V2<float> (&g)[Q]) {
+                                              V2<float> (&g)[Q], float& sr, float& sb) {
   using L = Lattice<Q>;
   using P = typename Storage<S>::packed;
   const Physics& ph = A.ph;
@@ -249,7 +264,8 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
     raw[i] = *reinterpret_cast<const uint32_t*>(&v);
   }
   const float2 r0 = restbox(ps[1], ey, ex);
-  g[0] = {r0.x, r0.y};
+  g[0] = {r0.x + r0.y, 0.0f};
+  float2 acc = r0;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const bool bounce = sbits && ((sbits >> i) & 1u);
@@ -260,21 +276,25 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
     const float2 d = Storage<S>::unpack(pv);
     const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
                                 __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
-    g[i] = {v.x, v.y};
+    acc = __fadd2_rn(acc, v);
+    g[i] = {v.x + v.y, 0.0f};
   }
+  sr = acc.x;
+  sb = acc.y;
 }
 
 // Recolour-on-pull layout: pull one cell's colour-blind populations and split each into its
 // colours with the source cell's record (w_r, V), staged in shared memory; recbox(q, y, x) as
 // restbox above.  f_i^r = w_r f_i + s_|c| (c_dir . V) with dir the stored direction (opp(i),
-// c_dir = -c_i, for a bounced link, whose source is the cell itself).  Each direction keeps its
-// own blue part f_i - f_i^r: the blue total is then a sum of small terms, not the difference of
-// two large ones (which would cost the density-ratio-10 case its FP32 tolerance).
+// c_dir = -c_i, for a bounced link, whose source is the cell itself).  Output as for
+// pull_cell_dev: g_i = (f_i, 0) and the colour totals; the blue total sums each direction's own
+// blue part f_i - f_i^r (small terms, not the difference of two large sums, which would cost the
+// density-ratio-10 case its FP32 tolerance).
 template <int Q, class RecBox>
 __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, int si,
                                              PlaneOffsets po, uint32_t sbits, int ex, int ey,
                                              const int (&ps)[3], const RecBox& recbox,
-                                             V2<float> (&g)[Q]) {
+                                             V2<float> (&g)[Q], float& sr, float& sb) {
   using L = Lattice<Q>;
   const float* pop = reinterpret_cast<const float*>(A.pin);
   float fv[Q];
@@ -293,9 +313,11 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
     fv[i] = __ldg(pop + (size_t)dir * A.g.nstore + src);
   }
   const float4 r0 = recbox(ps[1], ey, ex);
+  float2 acc;
   {
     const float fr = r0.x * fv[0];
-    g[0] = {fr, fv[0] - fr};
+    acc = make_float2(fr, fv[0] - fr);
+    g[0] = {fv[0], 0.0f};
   }
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
@@ -310,8 +332,11 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
     if (L::cm(i) < 0) cv -= r.w;
     if (bounce) cv = -cv;
     const float fr = fmaf(r.x, fv[i], float(rc_factor<L>(i)) * cv);
-    g[i] = {fr, fv[i] - fr};
+    acc = __fadd2_rn(acc, make_float2(fr, fv[i] - fr));
+    g[i] = {fv[i], 0.0f};
   }
+  sr = acc.x;
+  sb = acc.y;
 }
 
 template <class R>
@@ -544,7 +569,7 @@ struct TileSmem {
   // source staging: rest pairs (deviation storages) or recolouring records (ST_RC)
   static constexpr bool STAGE = DEV || S == ST_RC;
   static constexpr int BOX = S == ST_RC ? 16 : 8;
-  static constexpr int RX = STAGE ? TX + 4 : 1, RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1, RS = STAGE ? 3 : 1;
+  static constexpr int RX = STAGE ? TX + 4 : 1, RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1, RS = STAGE ? 4 : 1;
   // every part starts on a 16-byte boundary
   static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
   static constexpr int REST = ((RS * RY * RX * BOX) + 15) & ~15;
@@ -588,7 +613,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   constexpr bool STAGE = DEV || RCIN;    // pulls read per-source data staged in shared memory
   constexpr int RX = STAGE ? TX + 4 : 1;
   constexpr int RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1;
-  constexpr int RS = STAGE ? 3 : 1;
+  constexpr int RS = STAGE ? 4 : 1;  // planes m-1 .. m+2: one staged ahead, no extra barrier
   constexpr int RN = RX * RY;
   constexpr int RPT = (RN + NT - 1) / NT;  // rest-box elements staged per thread
   float2(*rest_ring)[RY][RX] = reinterpret_cast<float2(*)[RY][RX]>(rest_mem);
@@ -657,7 +682,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
     }
   }
   const int plane_stride = G.rows * G.pitch;
-  auto rest_slot = [&](int uq) { return (uq - m0 + 3) % 3; };
+  auto rest_slot = [&](int uq) { return (uq - m0 + 4) & 3; };
   // ST_RC: the recolouring records (w_r, V) of the same box, staged the same way
   float4(*rec_ring)[RY][RX] = reinterpret_cast<float4(*)[RY][RX]>(rest_mem);
   auto stage_rest = [&](int uq) {  // rest pairs / records of plane uq (unwrapped) into its slot
@@ -680,6 +705,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         const int e = tid + k * NT;
         if (e < RN && q.ok && rest_off[k] >= 0)
           rest_ring[sl][e / RX][e % RX] = __ldg(rest + q.m * plane_stride + rest_off[k]);
+      }
+    }
+  };
+  // the same staging split in two: the loads of plane uq into registers (issued before the
+  // pulls of a plane, so their latency overlaps them) and their stores into its slot (after)
+  using BoxT = typename std::conditional<RCIN, float4, float2>::type;
+  auto stage_load = [&](int uq, BoxT (&v)[RPT]) {
+    if constexpr (STAGE) {
+      const Plane q = make_plane(G, uq);
+      const BoxT* src = reinterpret_cast<const BoxT*>(reinterpret_cast<const char*>(A.pin) +
+                                                      (RCIN ? rc_record_offset(Q, G.nstore) : 0));
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int e = tid + k * NT;
+        if (e < RN && q.ok && rest_off[k] >= 0) v[k] = __ldg(src + q.m * plane_stride + rest_off[k]);
+      }
+    }
+  };
+  auto stage_store = [&](int uq, const BoxT (&v)[RPT]) {
+    if constexpr (STAGE) {
+      const Plane q = make_plane(G, uq);
+      BoxT(*ring_t)[RY][RX] = reinterpret_cast<BoxT(*)[RY][RX]>(rest_mem);
+      const int sl = rest_slot(uq);
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int e = tid + k * NT;
+        if (e < RN && q.ok && rest_off[k] >= 0) ring_t[sl][e / RX][e % RX] = v[k];
       }
     }
   };
@@ -711,12 +763,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
     const PlaneOffsets po = plane_offsets(G, p.m);
     const int slot = (um - m0 + 1) & 3;
     int ps[3] = {0, 0, 0};
-    if (STAGE) {  // the pulls of plane um read the staged data of planes um-1 .. um+1
-      stage_rest(um + 1);
-      __syncthreads();
+    BoxT staged[RPT];
+    if (STAGE) {  // the pulls of plane um read the staged data of planes um-1 .. um+1, staged
+                  // before the barrier that ended the previous plane
       ps[0] = rest_slot(um + 1);
       ps[1] = rest_slot(um);
       ps[2] = rest_slot(um - 1);
+      if constexpr (DEV) stage_load(um + 2, staged);  // registers to spare: load early
     }
     if (has_halo) {
       const int cell = (p.m * G.nb + hs.b) * G.na + hs.a;
@@ -726,15 +779,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         V2<R> tmp[Q];
         R t_rr, t_rb, t_e, t_irho;
         uint32_t t_flags;
-        if constexpr (DEV)
-          pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
-                              L::D3 ? hy + 1 : 0, ps, restbox, tmp);
-        else if constexpr (RCIN)
-          pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1, L::D3 ? hy + 1 : 0,
-                          ps, recbox, tmp);
-        else
+        if constexpr (STAGE) {  // colour-blind values and colour totals
+          R sr, sb;
+          if constexpr (DEV)
+            pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
+                                L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb);
+          else
+            pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
+                            L::D3 ? hy + 1 : 0, ps, recbox, tmp, sr, sb);
+          rn = exchange_from_sums<S>(A, cell, sr, sb, t_rr, t_rb, t_e, t_flags, t_irho);
+        } else {
           pull_cell<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, tmp);
-        rn = site_exchange<Q, S>(A, cell, tmp, t_rr, t_rb, t_e, t_flags, t_irho);
+          rn = site_exchange<Q, S>(A, cell, tmp, t_rr, t_rb, t_e, t_flags, t_irho);
+        }
       }
       ring[slot][hy][hx] = rn;
     }
@@ -746,12 +803,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       out[c].ok = solid_bits<L>(G, me[c], p, cells[c], bits);
       out[c].bits = bits;
       if (out[c].ok) {
+        // staged storages: g holds the colour-blind values, out.rr / out.rb the colour totals
         if constexpr (DEV)
           pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
-                              L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c]);
+                              L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c], out[c].rr,
+                              out[c].rb);
         else if constexpr (RCIN)
           pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
-                          L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c]);
+                          L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c], out[c].rr, out[c].rb);
         else
           pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
       }
@@ -759,15 +818,28 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       R rn = R(0);
-      if (out[c].ok)
-        rn = site_exchange<Q, S>(A, cells[c], g[c], out[c].rr, out[c].rb, out[c].e, out[c].flags,
-                                 out[c].irho);
+      if (out[c].ok) {
+        if constexpr (STAGE)
+          rn = exchange_from_sums<S>(A, cells[c], out[c].rr, out[c].rb, out[c].rr, out[c].rb,
+                                     out[c].e, out[c].flags, out[c].irho);
+        else
+          rn = site_exchange<Q, S>(A, cells[c], g[c], out[c].rr, out[c].rb, out[c].e,
+                                   out[c].flags, out[c].irho);
+      }
       ring[slot][ly0 + c * TY + OB][lx + 1] = rn;
     }
+    // plane um + 2 into the slot of plane um - 2, which the pulls of plane um - 1 read before
+    // the last barrier; the pulls of plane um + 1 read it after the next one
+    if constexpr (DEV)
+      stage_store(um + 2, staged);
+    else
+      stage_rest(um + 2);
   };
 
   stage_rest(m0 - 2);
   stage_rest(m0 - 1);
+  stage_rest(m0);
+  if (STAGE) __syncthreads();
   {
     CellScalars t[CPT];
     V2<R> g[CPT][Q];

@@ -27,8 +27,8 @@ template <int S>
 static KernelRef pick(int q, int variant) {
   if (q == 19) {
     switch (variant) {
-      case 0: return rc_ref<19, S, 32, 4, 4, 1>();
-      case 1: return rc_ref<19, S, 16, 8, 4, 1>();
+      case 0: return rc_ref<19, S, 16, 8, 4, 1>();  // the fastest: smallest staged box per cell
+      case 1: return rc_ref<19, S, 32, 4, 4, 1>();
       case 2: return rc_ref<19, S, 32, 4, 3, 1>();  // 168 registers, three CTAs per SM
       case 3: return rc_ref<19, S, 16, 4, 8, 1>();
       case 4: return rc_ref<19, S, 16, 8, 3, 1>();
