@@ -220,6 +220,22 @@ struct PopIO<ST_RCI, Q, false> {
 
 template <int S, int Q>
 struct PopIO<S, Q, true> {
+  // store() that also returns the rounding loss of the packed pair: (f - f0 kappa) scale minus
+  // what the stored 16-bit pair decodes to, in units of 1 / scale (exact in FP32 by Sterbenz's
+  // lemma: the stored value is zero or within a factor of two of the unrounded one)
+  static __device__ __forceinline__ float2 store_loss(void* base, int nstore, int i, int si,
+                                                      float r, float b, V2<float> f0,
+                                                      const Physics& ph) {
+    P* d = reinterpret_cast<P*>(reinterpret_cast<char*>(base) + dev_block_offset(nstore)) +
+           (size_t)(i - 1) * nstore + si;
+    const float2 dev = __fmul2_rn(
+        __ffma2_rn(make_float2(-f0.r, -f0.b), make_float2(ph.kap_r[i], ph.kap_b[i]), make_float2(r, b)),
+        make_float2(ph.scale, ph.scale));
+    const P h = Storage<S>::pack(dev.x, dev.y);
+    *d = h;
+    const float2 back = Storage<S>::unpack(h);
+    return make_float2(dev.x - back.x, dev.y - back.y);
+  }
   using R = float;
   using P = typename Storage<S>::packed;
   static __device__ __forceinline__ const float2* rest(const void* base) {

@@ -438,11 +438,15 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
         rc_pop[si + dimg[j]] = fi0;
         rc_rec[si + dimg[j]] = rec;
       }
-  } else {
+  } else if constexpr (!Storage<S>::dev) {
     IO::store(A.pout, A.g.nstore, 0, si, f0.r, f0.b, f0, ph);
     if (GHOSTS && nimg)
       for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0.r, f0.b, f0, ph);
   }
+  // deviation storages: the rounding loss of the 16-bit pairs, summed per colour (units of
+  // 1 / scale); the rest pair, stored last, takes it back so the cell's stored mass is its mass
+  float2 dev_loss = make_float2(0.0f, 0.0f);
+  (void)dev_loss;
   static_assert(opposites_adjacent<L>(), "directions (i, i+1), i odd, must be opposite");
   // Opposite directions (i, i+1) share |c.u|, |c.F| with opposite signs: the even part of Eq.
   // (feq) and the perturbation are common, the odd part of Eq. (feq) and the recoloring term
@@ -490,6 +494,16 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
           rc_pop[i * ns + si + dimg[k]] = fi;
           rc_pop[j * ns + si + dimg[k]] = fj;
         }
+    } else if constexpr (Storage<S>::dev) {
+      const float2 li = IO::store_loss(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
+      const float2 lj = IO::store_loss(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
+      dev_loss = __fadd2_rn(dev_loss, __fadd2_rn(li, lj));
+      if (GHOSTS && nimg) {
+        for (int k = 0; k < nimg; ++k) {
+          IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
+          IO::store(A.pout, A.g.nstore, j, si + dimg[k], frj, fj - frj, f0, ph);
+        }
+      }
     } else {
       IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
       IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
@@ -500,6 +514,16 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
         }
       }
     }
+  }
+  if constexpr (Storage<S>::dev) {
+    // decoding gives f_i = f_0 kappa_i + deviation / scale, so raising f_0^k by delta raises the
+    // cell's decoded mass by delta / phi_0(alpha_k) = delta / alpha_k; the moving pairs lost
+    // dev_loss / scale of mass: delta = alpha_k dev_loss / scale restores it exactly
+    const V2<R> f0c{fma(PHYS(R, ph, alpha_r) * R(ph.inv_scale), dev_loss.x, f0.r),
+                    fma(PHYS(R, ph, alpha_b) * R(ph.inv_scale), dev_loss.y, f0.b)};
+    IO::store(A.pout, A.g.nstore, 0, si, f0c.r, f0c.b, f0c, ph);
+    if (GHOSTS && nimg)
+      for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0c.r, f0c.b, f0c, ph);
   }
   Fn_out = Fn;
 }
