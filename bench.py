@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time K eager cgevap_step launches instead of one CUDA-graph replay of them")
     ap.add_argument("--kernel", type=int, default=-1, help="-1 auto, 0 register, 1 TMA pipeline")
     ap.add_argument("--variant", type=int, default=0, help="tile / pipeline variant of the kernel")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -460,15 +462,24 @@ def run_ours(args, d: Dist):
             sim.set_flux(case.phi)
             sim.init_equilibrium(rn, noise)
             sim.step(args.warmup)
+            graph = None
+            if not args.no_graph:  # the K launches captured once, replayed as one graph
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=stream):
+                    sim.step(K)
             torch.cuda.synchronize()
             d.barrier()
             clocks = Clocks(d.local_rank, enabled=(st == storages[0] and not args.no_clocks))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sim.step(K)
+            if graph is not None:
+                graph.replay()
+            else:
+                sim.step(K)
             e1.record(stream)
             torch.cuda.synchronize()
+            del graph
             clk = clocks.stop()
             d.barrier()
             ms = e0.elapsed_time(e1)
@@ -549,6 +560,8 @@ def run_ours(args, d: Dist):
         "scaling": "weak", "vs_baseline": None, "dtype": head if head != "f16dev" else "f32",
         "data": "synthetic",
         "config": {"workload": describe(case), "cells": cells, "storage": head,
+                   "timing": ("K eager step launches" if args.no_graph else
+                              "the K step launches captured in one CUDA graph, one replay timed"),
                    "parallelism": f"{d.world} independent replicas" if d.world > 1 else "1 GPU",
                    "l2": "no flush: the state (2 x %.2f GB) is larger than L2" % (
                        H["bytes_per_update"] * cells / 2 / 1e9)},
