@@ -316,7 +316,9 @@ CGEVAP_API const char* cgevap_ensemble_last_error(const cgevap_ens* ens);
 /* Number of members / total cells of all members. */
 CGEVAP_API int cgevap_ensemble_size(const cgevap_ens* ens);
 CGEVAP_API long long cgevap_ensemble_cells(const cgevap_ens* ens);
-/* Handle of member j (owned by the ensemble; do not destroy it or change its stream). */
+/* Handle of member j (owned by the ensemble; do not destroy it or change its stream).  Members
+ * take a scalar flux or a flux field; cgevap_ensemble_step fails with UNSUPPORTED while a member
+ * has outlets (cgevap_set_outlets) or a heated flux (cgevap_set_flux_heated) set. */
 CGEVAP_API int cgevap_ensemble_member(cgevap_ens* ens, int j, cgevap_sim** out);
 /* Stream for the ensemble and all its members (NULL = legacy default stream). */
 CGEVAP_API int cgevap_ensemble_set_stream(cgevap_ens* ens, void* cuda_stream);

@@ -20,6 +20,7 @@
 
 #include "../../include/cgevap.h"
 #include "launch.h"
+#include "sim.h"
 #include "step_kernel.cuh"
 
 using namespace cgevap;
@@ -508,6 +509,9 @@ int cgevap_ensemble_step(cgevap_ens* e, int nsteps) {
   if (!e || nsteps < 0) return CGEVAP_ERR_ARG;
   if (nsteps == 0) return CGEVAP_OK;
   EN_CUDA(e, cudaSetDevice(e->device));
+  for (cgevap_sim* s : e->sims)  // per-step work the persistent kernel does not do
+    if (s->outlet_rho[0] > 0.0 || s->outlet_rho[1] > 0.0 || s->heat.on)
+      return efail(e, CGEVAP_ERR_UNSUPPORTED, "ensemble members run neither outlets nor a heated flux");
   // the member table carries each member's flux, physics and solids of the moment, and the
   // buffer each state sits in; refresh both before the (graph) launch
   for (int j = 0; j < e->n; ++j) {

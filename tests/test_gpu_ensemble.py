@@ -107,3 +107,25 @@ def test_tunings_agree_and_autotune_restores_state():
         assert err <= 1e-6, (j, err)
     ens.close()
     ref.close()
+
+
+def test_members_refuse_outlets_and_heated_flux():
+    """The persistent kernel steps members as plain lattices: a member with outlets or a heated
+    flux makes the ensemble step fail loudly instead of ignoring them."""
+    from paper_2412_14859_gb300.binding import CgevapError, Ensemble
+    cases = [inputs.sessile_cap_3d((16, 24, 24), R0=6.0, phi0=1e-5),
+             inputs.sessile_cap_3d((16, 24, 24), R0=5.0, phi0=1e-5)]
+    ens = Ensemble(cases)
+    for c, m in zip(cases, ens.members):
+        m.set_flux(c.phi)
+        m.init_equilibrium(torch.from_numpy(c.phase()).cuda())
+    ens.step(2)
+    ens.members[0].set_outlets(1.0, 0.0)
+    with pytest.raises(CgevapError, match="UNSUPPORTED"):
+        ens.step(1)
+    ens.members[0].set_outlets(0.0, 0.0)
+    ens.members[1].set_flux_heated(1e-3, 0.5, 6.0, 1)
+    with pytest.raises(CgevapError, match="UNSUPPORTED"):
+        ens.step(1)
+    ens.members[1].set_flux(1e-5)
+    ens.step(1)
