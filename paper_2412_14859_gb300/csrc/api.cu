@@ -494,7 +494,7 @@ int cgevap_set_flux_heated(cgevap_sim* s, double phi_s, double K, double length,
   CG_CUDA(s, cudaSetDevice(s->device));
   const HeatedPlan hp = heated_plan(s->geom);
   if (!s->heat.part &&
-      cudaMalloc(&s->heat.part, (size_t)hp.nchunk * s->geom.na * s->geom.nb * sizeof(double)) != cudaSuccess)
+      cudaMalloc(&s->heat.part, (size_t)(hp.nchunk + 1) * s->geom.na * s->geom.nb * sizeof(double)) != cudaSuccess)
     return fail(s, CGEVAP_ERR_OOM, "cannot allocate the column partials");
   const bool dbl = s->p.storage == CGEVAP_F64;
   if (!s->phi_field && cudaMalloc(&s->phi_field, s->N * (dbl ? 8 : 4)) != cudaSuccess)

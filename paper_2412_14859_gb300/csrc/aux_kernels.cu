@@ -314,16 +314,25 @@ __global__ void k_column_liquid(Geom g, Physics ph, const void* state, int cz, d
   part[(size_t)blockIdx.y * ncol + col] = h;
 }
 
-// Second pass: h of the column = the chunk partials summed in chunk order (deterministic), and
-// every cell of planes [y*cz, y*cz + cz) of the column takes phi_s / (K + h / length).
-__global__ void k_heated_field(Geom g, const double* part, int nchunk, int cz, double phi_s, double K,
-                               double inv_length, void* field, int field_double) {
+// Second pass, per column: h = the chunk partials summed in chunk order (deterministic) and the
+// column's flux phi_s / (K + h / length), into row nchunk of part.
+__global__ void k_heated_column(Geom g, double* part, int nchunk, double phi_s, double K,
+                                double inv_length) {
   const int ncol = g.na * g.nb;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= ncol) return;
   double h = 0.0;
   for (int c = 0; c < nchunk; ++c) h += part[(size_t)c * ncol + col];
-  const double v = phi_s / (K + h * inv_length);
+  part[(size_t)nchunk * ncol + col] = phi_s / (K + h * inv_length);
+}
+
+// Third pass: every cell of planes [y*cz, y*cz + cz) of the column takes the column's flux.
+__global__ void k_heated_field(Geom g, const double* part, int nchunk, int cz, void* field,
+                               int field_double) {
+  const int ncol = g.na * g.nb;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  const double v = part[(size_t)nchunk * ncol + col];
   const int m0 = blockIdx.y * cz;
   const int m1 = min(g.nm, m0 + cz);
   for (int m = m0; m < m1; ++m) write_any(field, field_double ? 0 : 1, (size_t)m * ncol + col, v);
@@ -371,50 +380,49 @@ __device__ __forceinline__ void store_blue(void* state, const Geom& g, const Phy
 template <int Q, int S>
 __global__ void k_outlet(Geom g, Physics ph, void* state, double rho_lo, double rho_hi) {
   using L = Lattice<Q>;
+  using R = typename Storage<S>::real;  // the storage's arithmetic, as in the step
   const int ncol = g.na * g.nb;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * ncol; t += gridDim.x * blockDim.x) {
     const int side = t / ncol;
-    const double rho0 = side ? rho_hi : rho_lo;
-    if (!(rho0 > 0.0)) continue;
+    const R rho0 = (R)(side ? rho_hi : rho_lo);
+    if (!(rho0 > R(0))) continue;
     const int col = t - side * ncol;
-    Coord c;
-    c.a = col % g.na;
-    c.b = col / g.na;
-    c.m = side ? g.nm - 1 : 0;
-    if (cell_solid(g, c.m * ncol + col)) continue;
+    const int a = col % g.na, b = col / g.na, m = side ? g.nm - 1 : 0;
+    const int cell = m * ncol + col;
+    const uint32_t links = g.links ? __ldg(g.links + cell) : 0u;
+    if (links >> 31) continue;  // a solid cell
     const int inward = side ? -1 : 1;
-    const int si = sidx(g, c.a, c.b, c.m);
-    double gb[Q];
+    const int si = sidx(g, a, b, m);
+    R gb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      int src = neighbour(g, c, -L::ca(i), -L::cb(i), -L::cm(i));
-      if (src >= 0 && cell_solid(g, src)) src = -1;
-      if (src < 0) {
-        gb[i] = (double)PopIO<S, Q>::load(state, g.nstore, i, opp(i), si, ph).b;
-      } else {
-        const Coord sc = coord_of(g, src);
-        gb[i] = (double)PopIO<S, Q>::load(state, g.nstore, i, i, sidx(g, sc.a, sc.b, sc.m), ph).b;
-      }
+      const int sa = step_coord(a, -L::ca(i), g.na, g.per_a);
+      const int sb = step_coord(b, -L::cb(i), g.nb, g.per_b);
+      const int sm = step_coord(m, -L::cm(i), g.nm, g.per_m);
+      const bool bounce = sa < 0 || sb < 0 || sm < 0 || ((links >> i) & 1u);
+      gb[i] = bounce ? PopIO<S, Q>::load(state, g.nstore, i, opp(i), si, ph).b
+                     : PopIO<S, Q>::load(state, g.nstore, i, i, sidx(g, sa, sb, sm), ph).b;
     }
-    double s0 = 0.0, sout = 0.0, ta = 0.0, tb = 0.0;
+    R s0 = R(0), sout = R(0), ta = R(0), tb = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int cn = L::cm(i) * inward;
       if (cn == 0) {
         s0 += gb[i];
-        ta += L::ca(i) * gb[i];
-        tb += L::cb(i) * gb[i];
+        ta += R(L::ca(i)) * gb[i];
+        tb += R(L::cb(i)) * gb[i];
       } else if (cn < 0) {
         sout += gb[i];
       }
     }
-    const double un = 1.0 - (s0 + 2.0 * sout) / rho0;
-    const Images im = images_of(g, c.a, c.b, c.m);
+    const R un = R(1) - (s0 + R(2) * sout) / rho0;
+    const Images im = images_of(g, a, b, m);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (L::cm(i) * inward <= 0) continue;
-      const double v = gb[opp(i)] + 6.0 * L::W(i) * rho0 * un - (L::ca(i) * 0.5 * ta + L::cb(i) * 0.5 * tb);
-      for (int j = 0; j < im.n; ++j) store_blue<S>(state, g, ph, opp(i), im.s[j], v);
+      const R v = gb[opp(i)] + R(6.0 * L::W(i)) * rho0 * un -
+                  (R(L::ca(i)) * R(0.5) * ta + R(L::cb(i)) * R(0.5) * tb);
+      for (int j = 0; j < im.n; ++j) store_blue<S>(state, g, ph, opp(i), im.s[j], (double)v);
     }
   }
 }
@@ -501,7 +509,7 @@ cudaError_t launch_fill_ghosts(const AuxArgs& a, void* state, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-HeatedPlan heated_plan(const Geom& g) {
+HeatedPlan heated_plan(const Geom& g) {  // part: nchunk rows of partials + one of fluxes
   HeatedPlan hp;
   const int ncol = g.na * g.nb;
   hp.col_blocks = (ncol + kThreads - 1) / kThreads;
@@ -518,8 +526,8 @@ cudaError_t launch_heated_flux(const AuxArgs& a, const void* state, double* part
   const HeatedPlan hp = heated_plan(a.g);
   const dim3 grid((unsigned)hp.col_blocks, (unsigned)hp.nchunk);
   CGEVAP_DISPATCH(a, k_column_liquid, grid, s, a.g, a.ph, state, hp.cz, part);
-  k_heated_field<<<grid, kThreads, 0, s>>>(a.g, part, hp.nchunk, hp.cz, phi_s, K, 1.0 / length, field,
-                                           field_double);
+  k_heated_column<<<hp.col_blocks, kThreads, 0, s>>>(a.g, part, hp.nchunk, phi_s, K, 1.0 / length);
+  k_heated_field<<<grid, kThreads, 0, s>>>(a.g, part, hp.nchunk, hp.cz, field, field_double);
   return cudaGetLastError();
 }
 

@@ -75,7 +75,7 @@ cudaError_t launch_outlets(const AuxArgs& a, void* state, double rho_lo, double 
 
 // Heated-substrate flux field (aux_kernels.cu; Sec. III.C, Eq. heated): every cell of a column
 // along the march axis (the wall normal) takes phi_s / (K + h / length), h = the column's summed
-// liquid fraction.  `part` holds heated_plan(g).nchunk * na * nb doubles; field is double
+// liquid fraction.  `part` holds (heated_plan(g).nchunk + 1) * na * nb doubles; field is double
 // (field_double = 1) or float, [N].
 struct HeatedPlan {
   int col_blocks = 1, cz = 1, nchunk = 1;
