@@ -109,3 +109,22 @@ def test_heated_error_paths():
     periodic = Sim.from_case(inputs.sphere_3d(16, R0=4.0), "f32")
     with pytest.raises(CgevapError, match="ARG"):
         periodic.set_flux_heated(PHI_S, K, L, 1)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_field_matches_oracle_2d(storage):
+    """D2Q9: the substrate normal is y (walls at both ends of y), columns run along y."""
+    shape = (1, 40, 64)
+    case = inputs.Case("heated2d", 9, shape, periodic=(1, 0, 1), R0=12.0, phi=0.0)
+    sim = Sim.from_case(case, storage)
+    sim.set_flux(0.0)
+    phase = inputs.sphere_phase(shape, (0.0, -0.5, 31.5), 12.0)
+    sim.init_equilibrium(torch.from_numpy(phase).cuda())
+    sim.step(15)
+    sim.set_flux_heated(PHI_S, K, L, every=2)
+    m = sim.macros()
+    want = laws.heated_flux_field(m["rho_r"].cpu().numpy(), m["rho_b"].cpu().numpy(), None, PHI_S, K,
+                                  L, axis=1)
+    got = sim.flux_field().cpu().numpy()
+    assert rel(got, want) <= TOL[storage]
+    assert got.max() / got.min() > 1.5
