@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(256)
       rr += f.r;
       rb += f.b;
     }
-    v += 0.5 * (1.0 + ((double)rr - (double)rb) / ((double)rr + (double)rb));
+    // the liquid fraction in the storage's arithmetic (an FP64 division per cell would hold the
+    // FP32 kernel to GB300's FP64 rate), summed in FP64
+    v += (double)(rr / (rr + rb));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);

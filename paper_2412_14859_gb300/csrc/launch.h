@@ -104,7 +104,7 @@ cudaError_t launch_adjoint_stencil(const AuxArgs& a, const void* aux, const void
 cudaError_t launch_adjoint_gather(const AuxArgs& a, const void* lam_g, const void* ab,
                                   void* lam_out, cudaStream_t s);
 // Liquid volume of a state into *out (FP64); part holds kVolumeBlocks doubles, *done starts at 0.
-constexpr int kVolumeBlocks = 608;
+constexpr int kVolumeBlocks = 152 * 16;  // 16 CTAs of 256 threads per SM: loads in flight
 cudaError_t launch_volume(const AuxArgs& a, const void* state, double* part, unsigned int* done,
                           double* out, cudaStream_t s);
 
