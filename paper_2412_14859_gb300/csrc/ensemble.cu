@@ -46,7 +46,7 @@ struct EnsArgs {
   double* part_removed;  // [2][nitems]
   long long* part_sites;  // [2][nitems]
   const int* cur;        // [nmembers] buffer holding each member's state at launch
-  unsigned int* bar;     // [2]: arrivals, generation
+  unsigned int* bar;     // [4]: arrivals, generation, work counters of even / odd steps
   int* status;
   int nsteps;
 };
@@ -96,7 +96,17 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
     double* pr = E.part_removed + (size_t)par * E.nitems;
     long long* ps = E.part_sites + (size_t)par * E.nitems;
     const int nwork = E.n3 + E.npack;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    // items are taken from a counter in list order (largest D3Q19 members first), so a CTA that
+    // finishes early takes the next one: the step ends when the work does, not when the CTA with
+    // the unluckiest static share does
+    unsigned int* const next = E.bar + 2 + par;
+    __shared__ int w_sh;
+    for (;;) {
+      if (tid == 0) w_sh = (int)atomicAdd(next, 1u);
+      __syncthreads();
+      const int w = w_sh;
+      __syncthreads();  // every thread has read w before thread 0 takes the next one
+      if (w >= nwork) break;
       long long n = 0;
       double d = 0.0;
       if (w < E.n3) {
@@ -157,6 +167,8 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
       }
     }
     grid_barrier(E.bar, E.status);
+    // this step's counter is next used two steps on, after one more barrier
+    if (blockIdx.x == 0 && tid == 0) E.bar[2 + par] = 0u;
     // a barrier that gave up ends the launch in every CTA (each waits at most once more)
     __shared__ int stop;
     if (tid == 0) stop = *(volatile int*)E.status;
@@ -408,6 +420,8 @@ int launch(cgevap_ens* e, int nsteps) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {&a};
+  // the work counters start at zero (a launch whose barrier gave up may have left them set)
+  EN_CUDA(e, cudaMemsetAsync(e->d_bar + 2, 0, 2 * sizeof(unsigned int), e->stream));
   EN_CUDA(e, cudaLaunchKernelExC(&cfg, kernel_for_groups(e->groups), args));
   return CGEVAP_OK;
 }
@@ -450,12 +464,12 @@ int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out
   }
   if (cudaMalloc(&e->d_members, n * sizeof(EnsMember)) != cudaSuccess ||
       cudaMalloc(&e->d_cur, n * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&e->d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&e->d_bar, 4 * sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess) {
     cgevap_ensemble_destroy(e);
     return CGEVAP_ERR_OOM;
   }
-  cudaMemset(e->d_bar, 0, 2 * sizeof(unsigned int));
+  cudaMemset(e->d_bar, 0, 4 * sizeof(unsigned int));
   cudaMemset(e->d_status, 0, sizeof(int));
   cudaMemset(e->d_cur, 0, n * sizeof(int));
   int rc = build_plan(e);
