@@ -618,7 +618,7 @@ int cgevap_ensemble_autotune(cgevap_ens* e, int probe_steps, double* best_ms) {
     cudaMemcpyAsync(bk_led[j], v.ledger, sizeof(DevLedger), cudaMemcpyDeviceToDevice, e->stream);
   }
   const int cand_g[] = {4, 2};
-  const int cand_p3[] = {8, 16, 32, 64};
+  const int cand_p3[] = {16, 32, 64, 128};
   const int cand_p2[] = {16, 32, 64};
   double best = 1e300;
   int bg = e->groups, b3 = e->pc3, b2 = e->pc2;
