@@ -293,18 +293,6 @@ void release(cgevap_sim* s) {
 }  // namespace
 
 namespace cgevap {
-// Internal view of a simulation for the ensemble driver (same library, not exported).
-struct SimView {
-  Geom g;
-  Physics ph;
-  void* state[2];
-  uint8_t* mask[2];
-  DevLedger* ledger;
-  int* cur;
-  cudaStream_t* stream;
-  size_t state_bytes;
-  long long ncell;
-};
 int sim_view(cgevap_sim* s, SimView* v) {
   if (!s || !v) return CGEVAP_ERR_ARG;
   v->g = s->geom;

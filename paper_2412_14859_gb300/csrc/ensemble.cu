@@ -242,21 +242,7 @@ struct cgevap_ens {
   std::string err;
 };
 
-// Internal accessors of a single simulation (api.cu).
-namespace cgevap {
-struct SimView {
-  Geom g;
-  Physics ph;
-  void* state[2];
-  uint8_t* mask[2];
-  DevLedger* ledger;
-  int* cur;
-  cudaStream_t* stream;
-  size_t state_bytes;
-  long long ncell;
-};
-int sim_view(cgevap_sim* s, SimView* v);
-}  // namespace cgevap
+
 
 namespace {
 

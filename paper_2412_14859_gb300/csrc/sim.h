@@ -72,6 +72,20 @@ StepArgs step_args(cgevap_sim* s);
 int refresh_gradient_sites(cgevap_sim* s);
 // Adjoint tape release (adjoint.cu), called when the handle is destroyed.
 void adjoint_release(cgevap_sim* s);
+// View of a simulation for the ensemble driver (ensemble.cu): geometry, physics with its FP32
+// mirrors, the state and site buffers, the ledger and where the current buffer index lives.
+struct SimView {
+  Geom g;
+  Physics ph;
+  void* state[2];
+  uint8_t* mask[2];
+  DevLedger* ledger;
+  int* cur;
+  cudaStream_t* stream;
+  size_t state_bytes;
+  long long ncell;
+};
+int sim_view(cgevap_sim* s, SimView* v);
 }  // namespace cgevap
 
 #define CG_CUDA(s, call)                                                                          \
