@@ -60,7 +60,10 @@ extern "C" {
 /* ---- population storage formats (internal layouts; all arithmetic as stated) ---- */
 #define CGEVAP_F64 0      /* FP64 storage, FP64 arithmetic                                     */
 #define CGEVAP_F32 1      /* FP32 storage, FP32 arithmetic                                     */
-#define CGEVAP_F16DEV 2   /* FP32 rest populations + FP16 deviations of the moving ones, FP32 */
+#define CGEVAP_F16DEV 2   /* FP32 rest populations + FP16 deviations of the moving ones from
+                             the rest state of the cell's own rest population, FP32 arithmetic;
+                             each step's encoder returns the 16-bit rounding loss to the rest
+                             population, so the stored mass of a cell is its mass */
 #define CGEVAP_BF16DEV 3  /* as F16DEV with BF16 deviations                                    */
 #define CGEVAP_F32RC 4    /* "recolour on pull": per cell the Q colour-blind post-collision
                              populations and one record (rho_r / rho, V) in FP32, from which the
