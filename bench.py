@@ -249,8 +249,9 @@ def run_reference(args, d: Dist):
     dt = time.perf_counter() - t0
     value = case.ncell * args.steps / dt / 1e6
     full = workload(args.size)
-    sample = (f"FP64 C oracle, one thread; each step is one timestep of the same physics on a "
-              f"{side}^3 box (drop R0={case.R0:g}) instead of {args.size}^3")
+    where = (f"the full {side}^3 box" if side == args.size else
+             f"a {side}^3 box (drop R0={case.R0:g}) instead of {args.size}^3")
+    sample = f"FP64 C oracle, one thread; each step is one timestep of the same physics on {where}
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
             "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
