@@ -251,7 +251,7 @@ def run_reference(args, d: Dist):
     full = workload(args.size)
     where = (f"the full {side}^3 box" if side == args.size else
              f"a {side}^3 box (drop R0={case.R0:g}) instead of {args.size}^3")
-    sample = f"FP64 C oracle, one thread; each step is one timestep of the same physics on {where}
+    sample = f"FP64 C oracle, one thread; each step is one timestep of the same physics on {where}"
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
             "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
