@@ -69,5 +69,8 @@ def test_invalid_params_rejected(lib, bad, needle):
 
 def test_null_handles_rejected(lib):
     assert lib.cgevap_step(None, 1) == -1
+    assert lib.cgevap_set_outlets(None, 1.0, 1.0) == -1
+    assert lib.cgevap_set_flux_heated(None, 1e-3, 0.5, 10.0, 1) == -1
+    assert lib.cgevap_get_flux_field(None, None) == -1
     assert lib.cgevap_destroy(None) == 0
     assert lib.cgevap_bytes_per_update(None) == 0.0
