@@ -41,10 +41,11 @@ __device__ __forceinline__ int pull_source(const Slot& sl, const PlaneOffsets& p
 // run them backwards.  fcb: colour-blind sums of the post-exchange populations (rho_r, rho_b
 // given separately); lam: dL/d(f^{r*}, f^{b*}) of this cell;
 // out: lg = dL/dg through this cell's own collision, lF = dL/dF.
-template <int Q, class R>
+// lam_at(i): lambda^{n+1} of direction i (loaded where it is used); lg_out(i, v): stores lg_i.
+template <int Q, class R, class LamAt, class LgOut>
 __device__ __forceinline__ void collide_adjoint(const Physics& ph, const R (&fcb)[Q], R rr, R rb,
-                                                R irho, const R (&rnb)[Q], const V2<R> (&lam)[Q],
-                                                V2<R> (&lg)[Q], R (&lF)[3]) {
+                                                R irho, const R (&rnb)[Q], const LamAt& lam_at,
+                                                const LgOut& lg_out, R (&lF)[3]) {
   using L = Lattice<Q>;
   const R rho = rr + rb;
   const R wr = rr * irho, wb = rb * irho;
@@ -128,8 +129,9 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const R (&fcb
     const R pert = Ws[c] * Fn * nc * nc - Cs[c] * Fn;  // perturbation shape, Eq. (perturb)
     const R fi = f[i] + itau * (feq - f[i]) + pamp * pert;  // post-perturbation
     // Eq. (recolor): f^{r*} = wr fi + rcol nrm restc nc, f^{b*} = fi - f^{r*}
-    const R d = lam[i].r - lam[i].b;
-    const R q = wr * d + lam[i].b;  // dL/dfi
+    const V2<R> li = lam_at(i);
+    const R d = li.r - li.b;
+    const R q = wr * d + li.b;  // dL/dfi
     A_wr += d * fi;
     A_rcol += d * nrm[c] * restc[c] * nc;
     A_restc[c] += d * rcol * nrm[c] * nc;
@@ -190,7 +192,7 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const R (&fcb
     if (L::cb(i) < 0) a -= Ajb;
     if (L::cm(i) > 0) a += Ajm;
     if (L::cm(i) < 0) a -= Ajm;
-    lg[i] = {a + A_rr, a + A_rb};
+    lg_out(i, V2<R>{a + A_rr, a + A_rb});
   }
 }
 
@@ -206,23 +208,19 @@ struct AdjointEpilogue {
     using Vec = typename Storage<S>::vec;
     const int ns = A.g.nstore;
     const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);
-    V2<R> lam[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const Vec v = __ldg(lin + (size_t)i * ns + si);
-      lam[i] = {v.x, v.y};
-    }
-    V2<R> lg[Q];
-    R lF[3];
-    collide_adjoint<Q, R>(A.ph, g, rr, rb, irho, rnb, lam, lg, lF);
     Vec* lout = reinterpret_cast<Vec*>(o.lam_g);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    auto lam_at = [&](int i) -> V2<R> {
+      const Vec v = __ldg(lin + (size_t)i * ns + si);
+      return {v.x, v.y};
+    };
+    auto lg_out = [&](int i, V2<R> v2) {
       Vec v;
-      v.x = lg[i].r;
-      v.y = lg[i].b;
+      v.x = v2.r;
+      v.y = v2.b;
       lout[(size_t)i * ns + si] = v;
-    }
+    };
+    R lF[3];
+    collide_adjoint<Q, R>(A.ph, g, rr, rb, irho, rnb, lam_at, lg_out, lF);
     R* ax = reinterpret_cast<R*>(o.aux);
     ax[si] = lF[0];
     ax[(size_t)ns + si] = lF[1];
@@ -233,7 +231,7 @@ struct AdjointEpilogue {
 };
 
 template <int Q, int S, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 256 / (TX * TY))
+__global__ void __launch_bounds__(TX* TY, (S == ST_F64 ? 256 : 384) / (TX * TY))
     cg_adjoint_local_kernel(const __grid_constant__ StepArgs A,
                             const __grid_constant__ AdjointOut O) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
