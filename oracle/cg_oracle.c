@@ -10,8 +10,8 @@
  *
  * The lattice weights A_i, B_i, C_i, W_i and zeta are not printed in the paper (it defers them
  * to Leclaire et al. 2017); the values below are the standard ones of that model and are checked
- * by brute-force identities in tests/test_oracle_lattice.py.  Readings of points the paper leaves
- * open are listed in DESIGN.md ("readings"); the ones this file implements:
+ * by brute-force identities in tests/test_oracle_lattice.py.  Points the paper leaves open are
+ * read as follows here:
  *   - a neighbour that is solid contributes rho^N of the evaluating cell to the gradient
  *     (neutral wetting);
  *   - cos(theta_i) of the recoloring term is 0 for the rest direction and where |F| = 0;
