@@ -62,8 +62,13 @@ extern "C" {
 #define CGEVAP_F32 1      /* FP32 storage, FP32 arithmetic                                     */
 #define CGEVAP_F16DEV 2   /* FP32 rest populations + FP16 deviations of the moving ones from
                              the rest state of the cell's own rest population, FP32 arithmetic;
-                             each step's encoder returns the 16-bit rounding loss to the rest
-                             population, so the stored mass of a cell is its mass */
+                             each step sums each colour's pulled mass without rounding error
+                             and sets the stored rest population so that the cell's stored mass
+                             of each colour equals that exact mass up to the final rounding of
+                             the rest population and of each decode (rounding losses of the FP32
+                             collision and of the 16-bit encode taken back) in kernel variants
+                             0, 2, 4 (D3Q19) and 1 (D2Q9); the others, the D2Q9 default among
+                             them, return the 16-bit encode loss only */
 #define CGEVAP_BF16DEV 3  /* as F16DEV with BF16 deviations                                    */
 #define CGEVAP_F32RC 4    /* "recolour on pull": per cell the Q colour-blind post-collision
                              populations and one record (rho_r / rho, V) in FP32, from which the

@@ -199,6 +199,23 @@ __device__ __forceinline__ PlaneOffsets plane_offsets(const Geom& g, int m) {
   return o;
 }
 
+// Error-free sums (Knuth's TwoSum; Dekker's Fast2Sum where |a| >= |b|): s = fl(a + b) and the
+// rounding error a + b - s, exact in round-to-nearest.  Used to carry each colour's mass of a
+// cell exactly through the 16-bit storages' step.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // fl(a - b), one rounding
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bb = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// hi += v with the error added to lo (|hi| >= |v| per component; else lo is approximate)
+__device__ __forceinline__ void fast_two_sum_acc(float2& hi, float2& lo, float2 v) {
+  const float2 s = __fadd2_rn(hi, v);
+  lo = __fadd2_rn(lo, sub2(v, sub2(s, hi)));
+  hi = s;
+}
+
 // Pull one cell (Eq. Stream, pull form).  Sources are the slot's wrap-aware in-plane offsets plus
 // the plane offsets; where the source is solid or beyond a wall the population leaving the cell
 // comes back reversed (halfway bounce-back).
@@ -236,12 +253,15 @@ __device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int
 // plane m - c_m of direction i is ps[1 + c_m].  The step needs of the pulled pairs only the
 // colour-blind values and the two colour totals (Eq. exchange changes the totals, not the
 // colour-blind rest population), so that is what comes out: g_i = (f_i^r + f_i^b, 0) and
-// (sr, sb) = the sums of each colour over i; Q + 2 live values instead of 2Q.
+// (sr, sb) = the sums of each colour over i; Q + 2 live values instead of 2Q.  (lr, lb) are the
+// rounding errors of those sums: sr + lr is the exact sum of the decoded values (the rest
+// population, summed first, is the largest term).
 template <int Q, int S, class RestBox>
 __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl, int si,
                                               PlaneOffsets po, uint32_t sbits, int ex, int ey,
                                               const int (&ps)[3], const RestBox& restbox,
-                                              V2<float> (&g)[Q], float& sr, float& sb) {
+                                              V2<float> (&g)[Q], float& sr, float& sb,
+                                              float& lr, float& lb) {
   using L = Lattice<Q>;
   using P = typename Storage<S>::packed;
   const Physics& ph = A.ph;
@@ -265,7 +285,7 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
   }
   const float2 r0 = restbox(ps[1], ey, ex);
   g[0] = {r0.x + r0.y, 0.0f};
-  float2 acc = r0;
+  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const bool bounce = sbits && ((sbits >> i) & 1u);
@@ -276,11 +296,13 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
     const float2 d = Storage<S>::unpack(pv);
     const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
                                 __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
-    acc = __fadd2_rn(acc, v);
+    fast_two_sum_acc(acc, lo, v);
     g[i] = {v.x + v.y, 0.0f};
   }
   sr = acc.x;
   sb = acc.y;
+  lr = lo.x;
+  lb = lo.y;
 }
 
 // Recolour-on-pull layout: pull one cell's colour-blind populations and split each into its
@@ -360,14 +382,19 @@ __device__ __forceinline__ void norm_pair<float>(float F2, float& Fn, float& iFn
 //   f_i^eq = rho (A_s + B_s abar) + rho W_s (3 cu + 9/2 cu^2 - 3/2 u^2)            (Eq. feq)
 //   (9/4)(sigma/tau)|F|[W_s (F.c_i)^2/|F|^2 - C_s] = kw_s (F.c_i)^2 - kc_s        (Eq. perturb)
 //   beta (rho_r rho_b / rho^2) cos(theta_i) f_i^eq(rho, 0) = kr_s (F.c_i)          (Eq. recolor)
-template <int Q, int S, bool GHOSTS = true>
+// EXACT (16-bit storages): rr + lr and rb + lb are the cell's exact post-exchange colour masses;
+// the rest pair, stored last, also takes back the rounding of the collision's FP32 outputs, so
+// the stored mass of each colour is that exact mass (to the rest pair's own rounding).
+template <int Q, int S, bool GHOSTS = true, bool EXACT = false>
 __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nimg, const int (&dimg)[3],
                                               const typename Storage<S>::real (&fcb)[Q],
                                               typename Storage<S>::real rr,
                                               typename Storage<S>::real rb,
                                               typename Storage<S>::real irho,
                                               const typename Storage<S>::real (&rnb)[Q],
-                                              typename Storage<S>::real& Fn_out) {
+                                              typename Storage<S>::real& Fn_out,
+                                              typename Storage<S>::real lr = 0,
+                                              typename Storage<S>::real lb = 0) {
   using L = Lattice<Q>;
   using R = typename Storage<S>::real;
   using IO = PopIO<S, Q>;
@@ -447,6 +474,10 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   // 1 / scale); the rest pair, stored last, takes it back so the cell's stored mass is its mass
   float2 dev_loss = make_float2(0.0f, 0.0f);
   (void)dev_loss;
+  // EXACT: the FP32 outputs summed per colour without rounding error, rest pair first
+  float2 out_hi = make_float2(float(f0.r), float(f0.b)), out_lo = make_float2(0.0f, 0.0f);
+  (void)out_hi;
+  (void)out_lo;
   static_assert(opposites_adjacent<L>(), "directions (i, i+1), i odd, must be opposite");
   // Opposite directions (i, i+1) share |c.u|, |c.F| with opposite signs: the even part of Eq.
   // (feq) and the perturbation are common, the odd part of Eq. (feq) and the recoloring term
@@ -495,9 +526,17 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
           rc_pop[j * ns + si + dimg[k]] = fj;
         }
     } else if constexpr (Storage<S>::dev) {
-      const float2 li = IO::store_loss(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
-      const float2 lj = IO::store_loss(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
-      dev_loss = __fadd2_rn(dev_loss, __fadd2_rn(li, lj));
+      const float2 vi = make_float2(fri, fi - fri), vj = make_float2(frj, fj - frj);
+      const float2 li = IO::store_loss(A.pout, A.g.nstore, i, si, vi.x, vi.y, f0, ph);
+      const float2 lj = IO::store_loss(A.pout, A.g.nstore, j, si, vj.x, vj.y, f0, ph);
+      if constexpr (EXACT) {  // the stored (decoded) mass: outputs minus the pairs' losses
+        const float2 ninv = make_float2(-ph.inv_scale, -ph.inv_scale);
+        fast_two_sum_acc(out_hi, out_lo, vi);
+        fast_two_sum_acc(out_hi, out_lo, vj);
+        out_lo = __ffma2_rn(__fadd2_rn(li, lj), ninv, out_lo);
+      } else {
+        dev_loss = __fadd2_rn(dev_loss, __fadd2_rn(li, lj));
+      }
       if (GHOSTS && nimg) {
         for (int k = 0; k < nimg; ++k) {
           IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
@@ -519,8 +558,19 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     // decoding gives f_i = f_0 kappa_i + deviation / scale, so raising f_0^k by delta raises the
     // cell's decoded mass by delta / phi_0(alpha_k) = delta / alpha_k; the moving pairs lost
     // dev_loss / scale of mass: delta = alpha_k dev_loss / scale restores it exactly
-    const V2<R> f0c{fma(PHYS(R, ph, alpha_r) * R(ph.inv_scale), dev_loss.x, f0.r),
-                    fma(PHYS(R, ph, alpha_b) * R(ph.inv_scale), dev_loss.y, f0.b)};
+    V2<R> f0c;
+    if constexpr (EXACT) {
+      // EXACT: delta = alpha_k times what the stored mass misses of the exact mass, (rr + lr)
+      // - (out_hi + out_lo); the high parts agree to a few ulps, so their difference is exact
+      const float2 miss = __fadd2_rn(sub2(make_float2(rr, rb), out_hi),
+                                     sub2(make_float2(lr, lb), out_lo));
+      const float2 c = __ffma2_rn(make_float2(PHYS(R, ph, alpha_r), PHYS(R, ph, alpha_b)), miss,
+                                  make_float2(f0.r, f0.b));
+      f0c = V2<R>{c.x, c.y};
+    } else {
+      f0c = V2<R>{fma(PHYS(R, ph, alpha_r) * R(ph.inv_scale), dev_loss.x, f0.r),
+                  fma(PHYS(R, ph, alpha_b) * R(ph.inv_scale), dev_loss.y, f0.b)};
+    }
     IO::store(A.pout, A.g.nstore, 0, si, f0c.r, f0c.b, f0c, ph);
     if (GHOSTS && nimg)
       for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0c.r, f0c.b, f0c, ph);
@@ -561,13 +611,14 @@ __device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d
 // keeps each f_i), rho_r, rho_b and the neighbour phase field rnb are at hand: Eq.
 // (collision) to Eq. (recolor) and the store, the site byte of this step and the ledger terms.
 struct StepEpilogue {
+  // (lr, lb): the rounding errors of rr, rb (16-bit storages: rr + lr is the exact mass)
   template <int Q, int S, class R>
   __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
                                        const int (&dimg)[3], const R (&f)[Q], R rr, R rb,
                                        R irho, R e, uint32_t flags, const R (&rnb)[Q],
-                                       int& n_sites, R& removed) const {
+                                       int& n_sites, R& removed, R lr = R(0), R lb = R(0)) const {
     R Fn;
-    collide_store<Q, S, false>(A, si, nimg, dimg, f, rr, rb, irho, rnb, Fn);  // no ghosts
+    collide_store<Q, S, false, true>(A, si, nimg, dimg, f, rr, rb, irho, rnb, Fn, lr, lb);  // no ghosts
     uint32_t mb = flags;
     if (A.ph.rule == 0) {
       const R d = Fn - PHYS(R, A.ph, threshold);
@@ -769,12 +820,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 
   struct CellScalars {
     R rr, rb, e, irho;
+    R lr, lb;  // 16-bit storages: rounding errors of rr, rb
     uint32_t flags, bits;
     bool ok;
   };
   CellScalars cur[CPT], nxt[CPT];
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), 0u, 0u, false};
+  for (int c = 0; c < CPT; ++c)
+    cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), R(0), R(0), 0u, 0u, false};
   // this thread's sites and removed mass (a sum over at most one cell column: the kernel's own
   // real type suffices; the FP64 total is formed below and in the block reduction)
   int nloc = 0;
@@ -804,10 +857,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         R t_rr, t_rb, t_e, t_irho;
         uint32_t t_flags;
         if constexpr (STAGE) {  // colour-blind values and colour totals
-          R sr, sb;
+          R sr, sb, lr_unused, lb_unused;
           if constexpr (DEV)
             pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
-                                L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb);
+                                L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb, lr_unused, lb_unused);
           else
             pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                             L::D3 ? hy + 1 : 0, ps, recbox, tmp, sr, sb);
@@ -831,7 +884,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         if constexpr (DEV)
           pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                               L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c], out[c].rr,
-                              out[c].rb);
+                              out[c].rb, out[c].lr, out[c].lb);
         else if constexpr (RCIN)
           pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                           L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c], out[c].rr, out[c].rb);
@@ -843,10 +896,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
     for (int c = 0; c < CPT; ++c) {
       R rn = R(0);
       if (out[c].ok) {
-        if constexpr (STAGE)
-          rn = exchange_from_sums<S>(A, cells[c], out[c].rr, out[c].rb, out[c].rr, out[c].rb,
-                                     out[c].e, out[c].flags, out[c].irho);
-        else
+        if constexpr (STAGE) {
+          const R sr = out[c].rr, sb = out[c].rb;
+          rn = exchange_from_sums<S>(A, cells[c], sr, sb, out[c].rr, out[c].rb, out[c].e,
+                                     out[c].flags, out[c].irho);
+          if constexpr (DEV) {  // the exchange's own rounding joins the sums' (TwoSum)
+            out[c].lr = __fadd_rn(out[c].lr, two_sum_err(sr, -out[c].e, out[c].rr));
+            out[c].lb = __fadd_rn(out[c].lb, two_sum_err(sb, out[c].e, out[c].rb));
+          }
+        } else
           rn = site_exchange<Q, S>(A, cells[c], g[c], out[c].rr, out[c].rb, out[c].e,
                                    out[c].flags, out[c].irho);
       }
@@ -916,9 +974,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         }
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
-      epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
-                              cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
-                              nloc, rem);
+      if constexpr (DEV)
+        epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
+                                cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
+                                nloc, rem, cur[c].lr, cur[c].lb);
+      else
+        epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
+                                cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
+                                nloc, rem);
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];
