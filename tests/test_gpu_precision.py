@@ -1,10 +1,12 @@
 """16-bit deviation storage (FP32 rest populations + FP16 / BF16 deviations of the moving ones,
 FP32 arithmetic, FP64 ledger) against the FP64 path on the same seeded inputs.
 
-The mass bound is the stated target for the mixed form: relative error of the red mass
-<= 1e-5 against FP64, for both formats (the encoder returns each pair's rounding loss to the FP32
-rest population, so a cell's stored mass is its mass); BF16's 8 mantissa bits show in a looser,
-stated bound on the density field.  The ledger (FP64 sum of phi / S-bar over sites) must agree
+The stated target for the mixed form is a relative error of the red mass <= 1e-5 against FP64.
+The default kernel carries each colour's mass exactly through the step (error-free sums, the
+rest pair set to the exact mass), so the bounds here are tighter: 1e-7 for FP16 and 2e-6 for
+BF16 (measured on this case: 4.7e-9 and 1.3e-7; the second kernel family, which only returns
+the 16-bit encode loss, gives about 1.5e-6).  BF16's 8 mantissa bits show in a looser, stated
+bound on the density field.  The ledger (FP64 sum of phi / S-bar over sites) must agree
 with FP64 up to sites decided differently near the threshold, and the red mass that left must
 match it."""
 import numpy as np
@@ -16,8 +18,8 @@ from paper_2412_14859_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {  # storage: (relative red-mass error, relative L-inf of rho_r)
-    "f16dev": (1e-5, 5e-3),
-    "bf16dev": (1e-5, 5e-2),
+    "f16dev": (1e-7, 5e-3),
+    "bf16dev": (2e-6, 5e-2),
 }
 
 
