@@ -66,9 +66,8 @@ extern "C" {
                              and sets the stored rest population so that the cell's stored mass
                              of each colour equals that exact mass up to the final rounding of
                              the rest population and of each decode (rounding losses of the FP32
-                             collision and of the 16-bit encode taken back) in kernel variants
-                             0, 2, 4 (D3Q19) and 1 (D2Q9); the others, the D2Q9 default among
-                             them, return the 16-bit encode loss only */
+                             collision and of the 16-bit encode taken back), in every kernel
+                             variant */
 #define CGEVAP_BF16DEV 3  /* as F16DEV with BF16 deviations                                    */
 #define CGEVAP_F32RC 4    /* "recolour on pull": per cell the Q colour-blind post-collision
                              populations and one record (rho_r / rho, V) in FP32, from which the

@@ -171,12 +171,14 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_dev_kernel(const __grid_
 
   struct CellScalars {
     R rr, rb, e, irho;
+    R lr, lb;  // rounding errors of rr, rb: rr + lr is the exact post-exchange red mass
     uint32_t flags, bits;
     bool ok;
   };
   CellScalars cur[CPT], nxt[CPT];
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), 0u, 0u, false};
+  for (int c = 0; c < CPT; ++c)
+    cur[c] = nxt[c] = CellScalars{R(0), R(0), R(0), R(0), R(0), R(0), 0u, 0u, false};
   long long n_sites = 0;
   double removed = 0.0;
 
@@ -218,8 +220,15 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_dev_kernel(const __grid_
         V2<R> g[Q];
         dev_decode<Q, S, RY, RX>(A.ph, raw[c], out[c].bits, lx + 2, L::D3 ? ly0 + c * TY + 2 : 0,
                                  ps, rest_ring, g);
-        rn = site_exchange<Q, S>(A, cells[c], g, out[c].rr, out[c].rb, out[c].e, out[c].flags,
-                                 out[c].irho);
+        // colour totals without rounding error (the rest pair first: the largest term), then
+        // Eq. (exchange) with its own rounding error (the collision re-decodes g)
+        float2 hi = make_float2(g[0].r, g[0].b), lo = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) fast_two_sum_acc(hi, lo, make_float2(g[i].r, g[i].b));
+        rn = exchange_from_sums<S>(A, cells[c], hi.x, hi.y, out[c].rr, out[c].rb, out[c].e,
+                                   out[c].flags, out[c].irho);
+        out[c].lr = __fadd_rn(lo.x, two_sum_err(hi.x, -out[c].e, out[c].rr));
+        out[c].lb = __fadd_rn(lo.y, two_sum_err(hi.y, out[c].e, out[c].rb));
       }
       ring[slot][ly0 + c * TY + OB][lx + 1] = rn;
     }
@@ -279,9 +288,12 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_dev_kernel(const __grid_
         rnb[i] = solid_nb ? ownrn : ring[s][ly + OB + L::cb(i)][lx + 1 + L::ca(i)];
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
-      R Fn;
-      collide_store<Q, S>(A, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], g, cur[c].rr,
-                          cur[c].rb, cur[c].irho, rnb, Fn);
+      R Fn, fcb[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fcb[i] = g[i].r + g[i].b;
+      collide_store<Q, S, true, true>(A, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], fcb,
+                                      cur[c].rr, cur[c].rb, cur[c].irho, rnb, Fn, cur[c].lr,
+                                      cur[c].lb);
       uint32_t mb = cur[c].flags;
       if (A.ph.rule == 0) {
         const R d = Fn - PHYS(R, A.ph, threshold);

@@ -4,9 +4,9 @@ FP32 arithmetic, FP64 ledger) against the FP64 path on the same seeded inputs.
 The stated target for the mixed form is a relative error of the red mass <= 1e-5 against FP64.
 The default kernel carries each colour's mass exactly through the step (error-free sums, the
 rest pair set to the exact mass), so the bounds here are tighter: 1e-7 for FP16 and 2e-6 for
-BF16 (measured on this case: 4.7e-9 and 1.3e-7; the second kernel family, which only returns
-the 16-bit encode loss, gives about 1.5e-6).  BF16's 8 mantissa bits show in a looser, stated
-bound on the density field.  The ledger (FP64 sum of phi / S-bar over sites) must agree
+BF16 (measured on this case: 4.7e-9 and 1.3e-7, both kernel families; returning only the 16-bit
+encode loss gave about 1.5e-6).  BF16's 8 mantissa bits show in a looser, stated bound on the
+density field.  The ledger (FP64 sum of phi / S-bar over sites) must agree
 with FP64 up to sites decided differently near the threshold, and the red mass that left must
 match it."""
 import numpy as np
