@@ -83,3 +83,66 @@ def test_reference_arm_line(oracle_lib):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["steps"] == 2 and line["warmup"] == 1
+
+
+def test_adjoint_section_times_a_second_iteration(monkeypatch):
+    """The adjoint section runs one untimed fit iteration (fresh device memory is slow to write
+    the first time) and reports the second; every handle it opens is closed.  The library and
+    the CUDA timing are replaced by stand-ins that record the calls."""
+    import torch
+    import paper_2412_14859_gb300.adjoint as adjoint
+    import paper_2412_14859_gb300.binding as binding
+    b = load_bench()
+    calls = []
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            pass
+
+        def record(self, s=None):
+            calls.append("event")
+
+        def elapsed_time(self, other):
+            return 10.0
+
+    class FakeSim:
+        fluid_cells, bytes_per_update = 1000, 309.0
+
+        def __init__(self, case):
+            self.shape, self.closed = case.shape, False
+            calls.append("open")
+
+        @classmethod
+        def from_case(cls, case, storage):
+            return cls(case)
+
+        def init_equilibrium(self, rn):
+            pass
+
+        def set_flux(self, phi, field=None):
+            pass
+
+        def adjoint_forward(self, T, K):
+            return torch.linspace(10.0, 9.0, T + 1, dtype=torch.float64)
+
+        def close(self):
+            self.closed = True
+            calls.append("close")
+
+    def history(sim, phi, T, K):
+        calls.append("iteration")
+        return 10.0 - torch.arange(T + 1, dtype=phi.dtype) * phi.mean()
+
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(binding, "Sim", FakeSim)
+    monkeypatch.setattr(adjoint, "volume_history", history)
+    out = b.run_adjoint(SimpleNamespace(adjoint_steps=8, adjoint_shape="8,16,16"),
+                        torch.device("cpu"))
+    assert calls.count("iteration") == 2
+    assert calls.count("open") == calls.count("close") == 3  # target, warm-up, timed
+    # the timed events belong to the second iteration: three after its open
+    last_open = len(calls) - 1 - calls[::-1].index("open")
+    assert calls[last_open + 1:].count("event") == 3
+    assert out["forward_ms"] == out["backward_ms"] == 10.0 and "untimed" in out["warmup"]
