@@ -146,3 +146,32 @@ def test_adjoint_section_times_a_second_iteration(monkeypatch):
     last_open = len(calls) - 1 - calls[::-1].index("open")
     assert calls[last_open + 1:].count("event") == 3
     assert out["forward_ms"] == out["backward_ms"] == 10.0 and "untimed" in out["warmup"]
+
+
+def test_clock_samples_are_summarised(tmp_path):
+    """The clock record of a timed region: median SM clock under load, the maximum clock and the
+    throttle reasons seen (nvidia-smi CSV, no header, no units), malformed lines skipped."""
+    b = load_bench()
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+
+    class Proc:  # stands in for the nvidia-smi sampler process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = b.Clocks(0, enabled=False)
+    c.proc, c.path = Proc(), str(path)
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()  # the sample file is removed
+    assert b.Clocks(0, enabled=False).stop() is None
