@@ -290,8 +290,11 @@ CGEVAP_API int cgevap_adjoint_forward(cgevap_sim* sim, int nsteps, int ckpt_ever
  *                on phi); NULL means 0;
  *   dev_dL_dphi  caller-owned FP64 [z][y][x], overwritten with dL/dphi(x): 0 at solid cells and
  *                at cells that were never a site.
- * May be called again for another dL/dV over the same recorded run.  Errors: ARG (no recorded
- * run, NULL dev_dL_dphi, the step's tuning changed since the forward run), CUDA. */
+ * May be called again for another dL/dV over the same recorded run.  The first sweep over a
+ * new tape is the first to write its K recomputed states; on device memory not written before
+ * those first writes are slow (about 16 GB/s measured on GB300), so a fit loop's first iteration
+ * takes longer than the next ones.  Errors: ARG (no recorded run, NULL dev_dL_dphi, the step's
+ * tuning changed since the forward run), CUDA. */
 CGEVAP_API int cgevap_adjoint_backward(cgevap_sim* sim, const double* dev_dL_dV,
                                        double* dev_dL_dphi);
 
