@@ -62,6 +62,9 @@ def parse():
                     help="only check the flux-fit gradient against finite differences (FP64)")
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="steps of the 64-member ensemble workload (0: skip)")
+    ap.add_argument("--steady-s", type=float, default=1.0,
+                    help="seconds of extra graph replays of the headline storage, timed one by "
+                         "one, reported beside the K-step figure (0: skip)")
     return ap.parse_args()
 
 
@@ -166,6 +169,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def steady_state(graph, stream, ms_first: float, K: int, seconds: float):
+    """Replays of the captured K-step graph, each timed with CUDA events on the launching stream,
+    until about `seconds` of device time: median and spread of the time per step."""
+    import torch
+    reps = int(min(200, max(3, seconds * 1e3 / max(ms_first, 1e-3))))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for a, b in evs:
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    per = sorted(a.elapsed_time(b) / K for a, b in evs)
+    return {"replays": reps, "steps": reps * K, "ms_per_step": round(statistics.median(per), 5),
+            "ms_per_step_min": round(per[0], 5), "ms_per_step_max": round(per[-1], 5),
+            "device_s": round(sum(per) * K / 1e3, 3)}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -208,41 +229,83 @@ def describe(case) -> str:
 
 # ------------------------------------------------------------------ CPU oracle timing -------
 
-def oracle_rate(side: int, steps: int):
-    """MLUPS of the FP64 C oracle (single thread) on a side^3 box of the same physics."""
+def oracle_params(case):
+    """The oracle's parameter set for a seeded workload case (same fields, oracle's own type)."""
     import oracle
-    from tests.harness import oracle_params
+    nz, ny, nx = case.shape
+    return oracle.Params(q=case.q, nx=nx, ny=ny, nz=nz, periodic=tuple(case.periodic),
+                         rho_r_in=case.rho_r_in, rho_b_in=case.rho_b_in, tau_r=case.tau_r,
+                         tau_b=case.tau_b, sigma=case.sigma, beta=case.beta,
+                         site_rule=case.site_rule, threshold=case.threshold, sbar=case.sbar,
+                         phi=case.phi)
+
+
+def host_cpu():
+    """Host core count (usable by this process) and CPU model."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return cores, model or "unknown"
+
+
+def oracle_rate(side: int, steps: int, omp: bool = False):
+    """MLUPS of the FP64 C oracle on a side^3 box of the same physics: one thread, or (omp) the
+    OpenMP build of the same source on all host cores."""
+    import oracle
     case = workload(side)
     p = oracle_params(case)
-    run = oracle.Run(p, oracle.init(p, case.phase(), None))
+    run = oracle.Run(p, oracle.init(p, case.phase(), None), omp=omp)
     t0 = time.perf_counter()
     run.step(steps)
     dt = time.perf_counter() - t0
     return case.ncell * steps / dt / 1e6, dt
 
 
-def cpu_baseline(target_s: float = 12.0):
-    side = 64
-    rate, dt = oracle_rate(side, 1)
-    steps = max(1, min(100, int(target_s / max(dt, 1e-3))))
-    rate, dt = oracle_rate(side, steps)
-    return {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, one thread, {steps} steps of the same physics on a {side}^3 "
-                      f"box (drop R0={32 * side / 192:g}), {dt:.1f} s"}
+def cpu_baseline(target_s: float = 10.0):
+    """The oracle timed on this host: one thread on a 64^3 box, and the OpenMP build of the same
+    source on all host cores on a 128^3 box; each sample sized to about target_s seconds."""
+    cores, model = host_cpu()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    out = {}
+    for omp, side in ((False, 64), (True, 128)):
+        rate, dt = oracle_rate(side, 1, omp)
+        steps = max(1, min(200, int(target_s / max(dt, 1e-3))))
+        rate, dt = oracle_rate(side, steps, omp)
+        out[omp] = (rate, dt, steps, side)
+    rate, dt, steps, side = out[True]
+    r1, dt1, steps1, side1 = out[False]
+    return {"value": round(rate, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": model, "nproc": cores,
+            "sample": f"FP64 C oracle built with OpenMP, {cores} threads, {steps} steps of the same "
+                      f"physics on a {side}^3 box (drop R0={32 * side / 192:g}), {dt:.1f} s",
+            "single_thread": {"value": round(r1, 4), "unit": UNIT, "cores": 1,
+                              "sample": f"the plain oracle build, one thread, {steps1} steps on a "
+                                        f"{side1}^3 box, {dt1:.1f} s"}}
 
 
 def run_reference(args, d: Dist):
     if d.rank != 0:
         return
     import oracle
-    from tests.harness import oracle_params
+    cores, model = host_cpu()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     # size the sample so warm-up + timed steps take about two minutes
-    probe, dt1 = oracle_rate(32, 1)
+    probe, dt1 = oracle_rate(48, 1, omp=True)
     budget = 120.0 / max(1, args.steps + args.warmup)
     side = int(max(12, min(args.size, round((budget * probe * 1e6) ** (1 / 3)))))
     case = workload(side)
     p = oracle_params(case)
-    run = oracle.Run(p, oracle.init(p, case.phase(), None))
+    run = oracle.Run(p, oracle.init(p, case.phase(), None), omp=True)
     run.step(args.warmup)
     t0 = time.perf_counter()
     run.step(args.steps)
@@ -251,14 +314,15 @@ def run_reference(args, d: Dist):
     full = workload(args.size)
     where = (f"the full {side}^3 box" if side == args.size else
              f"a {side}^3 box (drop R0={case.R0:g}) instead of {args.size}^3")
-    sample = f"FP64 C oracle, one thread; each step is one timestep of the same physics on {where}"
+    sample = (f"FP64 C oracle built with OpenMP, {cores} threads ({model}); each step is one "
+              f"timestep of the same physics on {where}")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
             "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe(full), "cells": full.ncell, "sample_cells": case.ncell},
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": model, "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -290,7 +354,19 @@ def run_ensemble(args, dev):
     ens.status()
     ms = e0.elapsed_time(e1)
     cells = ens.cells
+    # bytes-weighted roofline: each member's algorithmic bytes per update times its cells
+    c2 = sum(m.fluid_cells for m, c in zip(ens.members, cases) if c.q == 9)
+    c3 = sum(m.fluid_cells for m, c in zip(ens.members, cases) if c.q == 19)
+    nbytes = sum(m.fluid_cells * m.bytes_per_update for m in ens.members)
+    gbs = nbytes * args.ensemble_steps / (ms / 1e3) / 1e9
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
     out = {"mlups": round(cells * args.ensemble_steps / (ms / 1e3) / 1e6, 1), "cells": cells,
+           "cells_d2q9": c2, "cells_d3q19": c3,
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(gbs / hbm, 4),
+                        "algorithmic_bytes_per_step": nbytes,
+                        "note": "sum over members of cells x bytes per update (D2Q9 FP32 145 B, "
+                                "D3Q19 FP32 305 B, band rule)"},
            "members": len(cases), "steps": args.ensemble_steps,
            "ms_per_step": round(ms / args.ensemble_steps, 4), "tuning": ens.tuning(),
            "autotune_ms_per_step": round(best, 4),
@@ -489,21 +565,30 @@ def run_ours(args, d: Dist):
                 sim.step(K)
             e1.record(stream)
             torch.cuda.synchronize()
-            del graph
-            clk = clocks.stop()
-            d.barrier()
             ms = e0.elapsed_time(e1)
             mlups, ms_max = aggregate(sim.fluid_cells, K, ms, d)
             bpu = sim.bytes_per_update
             per_launch_s = ms / K / 1e3
             achieved = bpu * sim.fluid_cells / per_launch_s / 1e9
+            # the state after warm-up + K steps, compared across storages below
             m = sim.macros()
             rho_r[st] = m["rho_r"]
             led = sim.ledger()
+            mass_r = float(m["rho_r"].sum())
+            # headline storage: more replays of the same graph, each timed on its own, so that
+            # the fraction also rests on a region of about steady_s seconds (clocks still sampled)
+            steady = None
+            if st == storages[0] and graph is not None and args.steady_s > 0:
+                steady = steady_state(graph, stream, ms, K, args.steady_s)
+                steady["mlups"] = round(sim.fluid_cells / (steady["ms_per_step"] / 1e3) / 1e6, 1)
+                steady["frac"] = round(bpu * sim.fluid_cells / (steady["ms_per_step"] / 1e3) / 1e9 / hbm, 4)
+            del graph
+            clk = clocks.stop()
+            d.barrier()
             results[st] = {"mlups": mlups, "ms": ms_max, "bytes_per_update": bpu, "tuning": sim.tuning(),
                            "achieved_gbs": achieved, "frac": achieved / hbm, "clocks": clk,
-                           "mass_r": float(m["rho_r"].sum()), "ledger": led["evaporated"],
-                           "steps_total": led["steps"], "sim": sim}
+                           "mass_r": mass_r, "ledger": led["evaporated"],
+                           "steps_total": led["steps"], "sim": sim, "steady": steady}
         if st != storages[0]:
             sim.close()
             results[st]["sim"] = None
@@ -540,20 +625,33 @@ def run_ours(args, d: Dist):
             sim2.set_flux(case.phi)
             sim2.set_populations_host(f_host)  # allocates the staging buffer once, untimed
             sim2.step(args.warmup)  # untimed: both state buffers written once (warm memory)
+            warm = sim2.macros()    # untimed: the readout's device buffers come from the cache
+            out_host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                        for k, v in warm.items()}
+            del warm
             torch.cuda.synchronize()
             d.barrier()
+            # timed: the initial state from pinned host memory, K steps each followed by the
+            # ledger read (40 B), and the final macroscopic fields (rho_r, rho_b, u, rho^N in
+            # FP64) copied back into pinned host memory
             t0 = time.perf_counter()
             sim2.set_populations_host(f_host)
             for _ in range(args.steps):
                 sim2.step(1)
                 sim2.ledger()
+            fields = sim2.macros()
+            for k, v in fields.items():
+                out_host[k].copy_(v, non_blocking=True)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             d.barrier()
+            readback = sum(v.numel() * v.element_size() for v in out_host.values())
             e2e_mlups, _ = aggregate(sim2.fluid_cells, args.steps, dt * 1e3, d)
             e2e = {"value": round(e2e_mlups, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(f_host.nbytes // args.steps),
-                   "d2h_bytes_per_step": 40}
+                   "d2h_bytes_per_step": int((40 * args.steps + readback) // args.steps),
+                   "what": "pinned host state in, K steps each with a 40-byte ledger read, final "
+                           "rho_r, rho_b, u, rho^N (FP64) out; wall clock around it"}
             sim2.close()
     elif sim is not None:
         sim.close()
@@ -592,6 +690,8 @@ def run_ours(args, d: Dist):
         line["adjoint"] = adjoint
     if H["clocks"]:
         line["clocks"] = H["clocks"]
+    if H["steady"]:
+        line["steady_state"] = H["steady"]
     if e2e:
         line["e2e"] = e2e
     if d.world == 1 and not args.no_cpu_baseline:

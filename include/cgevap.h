@@ -16,7 +16,8 @@
  * Conventions for every function:
  *   - return 0 (CGEVAP_OK) on success or a negative CGEVAP_ERR_* code; nothing throws, aborts or
  *     exits across this boundary; cgevap_last_error(sim) gives a message for the last failure
- *     on that handle (cgevap_last_error(NULL) for failures of cgevap_create);
+ *     on that handle (cgevap_last_error(NULL) for failures of cgevap_create and of
+ *     cgevap_step_static_scratch on the calling thread);
  *   - pointers named dev_* are CUDA device pointers owned by the caller, host_* host pointers;
  *     inputs are copied into library-owned buffers, outputs are written into the caller's buffers;
  *   - work is enqueued on the handle's stream (cgevap_set_stream) and is asynchronous unless the
@@ -74,6 +75,20 @@ extern "C" {
                              next step forms each colour as Eq. (recolor) does; Q + 4 floats per
                              cell instead of 2Q, FP32 arithmetic.  An imported state (init,
                              set_populations) is held as FP32 pairs until the next step. */
+#define CGEVAP_F16RC 5    /* the populations of F32RC stored as FP16 deviations from the
+                             lattice-weight rest state of the cell, with FP32 arithmetic: per
+                             cell an FP32 rest pair (f_0^r, f_0^b), the FP32 record (rho_r / rho,
+                             V), an FP32 rest-state scale Rf and Q - 1 FP16 values
+                             s (f_i - r_i Rf) of the colour-blind post-collision populations
+                             (f_i^eq(rho, 0) = r_i Rf, r_i = A_i / A_1, s a power of two), which
+                             the next step splits into colours as Eq. (recolor) does.  Each
+                             step carries each colour's mass exactly: the pulled colour parts
+                             are summed without rounding error and the stored rest pair is set
+                             so that what a cell passes on of each colour equals its exact
+                             post-exchange mass up to the rounding of the rest pair.
+                             2 (28 + 2 (Q - 1)) + 1 bytes per lattice update (129 for D3Q19).
+                             An imported state is held as FP32 pairs until the next step. */
+#define CGEVAP_BF16RC 6   /* as F16RC with BF16 values (s = 1)                                */
 
 /* ---- element types of caller buffers ---- */
 #define CGEVAP_DTYPE_F64 0
@@ -91,7 +106,7 @@ typedef struct cgevap_params {
   int site_rule;          /* CGEVAP_SITES_GRADIENT, CGEVAP_SITES_BAND or CGEVAP_SITES_GIVEN     */
   double threshold;       /* Gamma (gradient rule) or theta (band rule)                       */
   double sbar;            /* S-bar > 0 of Eq. (relation); varphi = phi / S-bar                */
-  int storage;            /* CGEVAP_F64, CGEVAP_F32, CGEVAP_F16DEV, CGEVAP_BF16DEV or F32RC   */
+  int storage;            /* CGEVAP_F64, F32, F16DEV, BF16DEV, F32RC, F16RC or BF16RC        */
 } cgevap_params;
 
 typedef struct cgevap_ledger {
@@ -309,23 +324,32 @@ CGEVAP_API int cgevap_adjoint_release(cgevap_sim* sim);
 /* ---- ensembles: many independent lattices in one persistent launch ---------------------------
  * An ensemble advances n independent members (D2Q9 and D3Q19 lattices of any sizes, each with its
  * own densities, relaxation times, surface tension, recoloring, site rule, threshold, S-bar,
- * flux and solids; FP32 storage) by one cooperative persistent kernel launch per call, captured
+ * flux and solids; FP32 or FP64 storage, mixed freely) by one cooperative persistent kernel
+ * launch per call, captured
  * once in a CUDA graph and replayed.  Each member is a full cgevap_sim reachable with
  * cgevap_ensemble_member: set its flux, solids and initial state, read its macros, mask and
  * ledger with the single-lattice calls; cgevap_ensemble_step advances all of them together and
  * gives the same result per member as cgevap_step on that member alone. */
 typedef struct cgevap_ens cgevap_ens;
 
-/* Create members[0..n-1] (each validated like cgevap_create; storage must be CGEVAP_F32, else
- * UNSUPPORTED) and plan the work list with a default tiling.  *out is NULL on failure. */
+/* Create members[0..n-1] (each validated like cgevap_create; storage must be CGEVAP_F32 or
+ * CGEVAP_F64, else UNSUPPORTED) and plan the work list with a default tiling.  An ensemble whose
+ * members are all FP32 runs four CTAs per SM; one with FP64 members runs two (the FP64 step needs
+ * more registers).  *out is NULL on failure. */
 CGEVAP_API int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out);
 /* Free the ensemble and all its members.  NULL is accepted. */
 CGEVAP_API int cgevap_ensemble_destroy(cgevap_ens* ens);
 /* Message for the last failure on ens; never NULL. */
 CGEVAP_API const char* cgevap_ensemble_last_error(const cgevap_ens* ens);
-/* Number of members / total cells of all members. */
+/* Number of members / total cells of the active (not paused) members. */
 CGEVAP_API int cgevap_ensemble_size(const cgevap_ens* ens);
 CGEVAP_API long long cgevap_ensemble_cells(const cgevap_ens* ens);
+/* Pause (active = 0) or resume (1) member j: a paused member takes no part in the following
+ * cgevap_ensemble_step calls -- its state, site bytes and ledger stay as they are -- so a sweep
+ * whose members reach their end at different times stops spending the launch on the finished
+ * ones.  The work list is re-planned (the cached graph is rebuilt on the next step).  Errors: ARG
+ * (j out of range, active not 0/1, or pausing the last active member). */
+CGEVAP_API int cgevap_ensemble_set_active(cgevap_ens* ens, int j, int active);
 /* Handle of member j (owned by the ensemble; do not destroy it or change its stream).  Members
  * take a scalar flux or a flux field; cgevap_ensemble_step fails with UNSUPPORTED while a member
  * has outlets (cgevap_set_outlets) or a heated flux (cgevap_set_flux_heated) set. */
@@ -336,8 +360,22 @@ CGEVAP_API int cgevap_ensemble_set_stream(cgevap_ens* ens, void* cuda_stream);
  * replayed).  Asynchronous; cgevap_ensemble_status reports a grid barrier that gave up. */
 CGEVAP_API int cgevap_ensemble_step(cgevap_ens* ens, int nsteps);
 /* CGEVAP_ERR_TIMEOUT if a bounded grid barrier gave up since the last call (flag cleared), else
- * OK; synchronises the stream. */
+ * OK; synchronises the stream.  After a barrier gave up, the members' states are those of
+ * whatever steps their items completed: re-initialise or reload them before trusting them; the
+ * next launch starts with a clean barrier. */
 CGEVAP_API int cgevap_ensemble_status(cgevap_ens* ens);
+/* Limit of one grid-barrier wait of the persistent launch, in milliseconds (default 4000, >= 1).
+ * A wait that reaches it sets the status that cgevap_ensemble_status reports and every CTA
+ * leaves the launch at its next barrier.  Errors: ARG. */
+CGEVAP_API int cgevap_ensemble_set_barrier_timeout(cgevap_ens* ens, int ms);
+/* Test hook for the timeout path: in the following launches CTA `cta` (0 <= cta <
+ * cgevap_ensemble_grid) does not arrive at the grid barrier after step `step` of the launch, so
+ * the other CTAs wait until the barrier limit and the launch ends with CGEVAP_ERR_TIMEOUT; no
+ * memory is touched out of turn and every wait stays bounded.  cta = -1 turns it off.
+ * Errors: ARG. */
+CGEVAP_API int cgevap_ensemble_debug_skip_arrival(cgevap_ens* ens, int cta, int step);
+/* CTAs of the persistent launch of the current plan. */
+CGEVAP_API int cgevap_ensemble_grid(const cgevap_ens* ens);
 /* Tiling of the work list: D2Q9 tiles per CTA (2 or 4, i.e. rows of 128 or 64 cells) and planes
  * per chunk for D3Q19 and D2Q9 members. */
 CGEVAP_API int cgevap_ensemble_set_tuning(cgevap_ens* ens, int groups, int planes_3d, int planes_2d);
@@ -377,8 +415,11 @@ CGEVAP_API int cgevap_ensemble_autotune(cgevap_ens* ens, int probe_steps, double
  *   cuda_stream    stream to run on (NULL = legacy default stream).
  * Returns ARG for invalid parameters, NULL or aliasing buffers, a wrong state_bytes, or a lattice
  * whose grid exceeds 16384 CTAs; CUDA on a failed runtime call; otherwise OK (asynchronous).
+ * A failure's message is cgevap_last_error(NULL) (same thread).
  * The first call on each device resolves the scratch's device address (cudaGetSymbolAddress with
- * that device current); make that first call before any stream capture.  Every call on a device
+ * that device current); make that first call before any stream capture.  The address is resolved
+ * again when the device's current context has changed since (after cudaDeviceReset, for example;
+ * the scratch's contents are then new).  Every call on a device
  * shares the scratch: calls that overlap on the GPU (different streams, concurrent threads) race
  * and must be serialised by the caller.  The arrival counter in the scratch is cleared on the
  * stream before each launch; the partial sums need no clearing. */

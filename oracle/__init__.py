@@ -23,25 +23,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libcg_oracle.so")
+# The same source built with OpenMP: used only to time the oracle on all host cores (the CPU
+# baseline of bench.py); every test uses the single-thread library above.
+_SO_OMP = os.path.join(_BUILD, "libcg_oracle_omp.so")
 
 RULE_GRADIENT = 0
 RULE_BAND = 1
 RULE_GIVEN = 2  # replay a recorded site set (bit 0 of ``mask_given``)
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (plain gcc, IEEE FP64, no contraction into FMA)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the C oracle (plain gcc, IEEE FP64, no contraction into FMA); omp: the OpenMP
+    timing build of the same source instead."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+    so = _SO_OMP if omp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "cg_oracle.h"))
     ):
-        tmp = _SO + f".{os.getpid()}.tmp"
+        tmp = so + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-             "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+            + (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"]
         )
-        os.replace(tmp, _SO)
-    return _SO
+        os.replace(tmp, so)
+    return so
 
 
 class _Params(ctypes.Structure):
@@ -69,28 +74,38 @@ class _Ledger(ctypes.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
-def _L():
-    global _lib
+def _L(omp: bool = False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ctypes.CDLL(build(omp=True)))
+        return _lib_omp
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        up = ctypes.POINTER(ctypes.c_ubyte)
-        ip = ctypes.POINTER(ctypes.c_int)
-        pp = ctypes.POINTER(_Params)
-        _lib.orc_lattice.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp, dp, ip]
-        _lib.orc_alphas.argtypes = [pp, dp, dp]
-        _lib.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
-        _lib.orc_perturbation_shape.argtypes = [ctypes.c_int, dp, dp]
-        _lib.orc_init.argtypes = [pp, dp, dp, dp]
-        _lib.orc_gradient_norm.argtypes = [pp, dp, dp]
-        _lib.orc_step.argtypes = [pp, dp, dp, dp, dp, up, dp, ctypes.POINTER(_Ledger)]
-        _lib.orc_step_cells.argtypes = [pp, dp, dp, ctypes.POINTER(ctypes.c_longlong),
-                                        ctypes.c_longlong, dp, dp, up]
-        _lib.orc_macros.argtypes = [pp, dp, dp, dp, dp, dp]
-        _lib.orc_outlet_blue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument types of the exported oracle functions."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    up = ctypes.POINTER(ctypes.c_ubyte)
+    ip = ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(_Params)
+    lib.orc_lattice.argtypes = [ctypes.c_int, ip, dp, dp, dp, dp, dp, ip]
+    lib.orc_alphas.argtypes = [pp, dp, dp]
+    lib.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
+    lib.orc_perturbation_shape.argtypes = [ctypes.c_int, dp, dp]
+    lib.orc_init.argtypes = [pp, dp, dp, dp]
+    lib.orc_gradient_norm.argtypes = [pp, dp, dp]
+    lib.orc_step.argtypes = [pp, dp, dp, dp, dp, up, dp, ctypes.POINTER(_Ledger)]
+    lib.orc_step_cells.argtypes = [pp, dp, dp, ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.c_longlong, dp, dp, up]
+    lib.orc_macros.argtypes = [pp, dp, dp, dp, dp, dp]
+    lib.orc_outlet_blue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+    return lib
 
 
 def _dp(a: Optional[np.ndarray]):
@@ -225,10 +240,12 @@ def macros(p: Params, f: np.ndarray):
 
 
 class Run:
-    """A lattice advanced by the oracle: state f (post-recoloring), |F| of the last step, ledger."""
+    """A lattice advanced by the oracle: state f (post-recoloring), |F| of the last step, ledger.
+    omp: step with the OpenMP timing build (all host cores; for timing only)."""
 
-    def __init__(self, p: Params, f: np.ndarray):
+    def __init__(self, p: Params, f: np.ndarray, omp: bool = False):
         self.p = p
+        self.omp = omp
         self.f = np.ascontiguousarray(f, np.float64).copy()
         self.G = gradient_norm(p, self.f)  # |F| "of the previous step" before step 0
         self.mask = np.zeros(p.shape, np.uint8)
@@ -242,7 +259,7 @@ class Run:
         f_out = np.empty_like(self.f)
         G_out = np.empty(self.p.shape)
         for _ in range(n):
-            _check(_L().orc_step(ctypes.byref(cp), _dp(self.f), _dp(f_out), _dp(self.G),
+            _check(_L(self.omp).orc_step(ctypes.byref(cp), _dp(self.f), _dp(f_out), _dp(self.G),
                                  _dp(G_out), _up(self.mask), _dp(self.margin),
                                  ctypes.byref(self.ledger)))
             self.f, f_out = f_out, self.f

@@ -425,7 +425,9 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out, const doubl
     return -2;
   }
 
-  /* Streaming, Eq. (Stream), pull form. */
+  /* Streaming, Eq. (Stream), pull form.  (The omp pragmas only matter in the separately built
+     timing library of the CPU baseline; the pinned oracle is compiled without OpenMP.) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < p->nz; z++)
     for (int y = 0; y < p->ny; y++)
       for (int x = 0; x < p->nx; x++) {
@@ -440,6 +442,7 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out, const doubl
   /* Steps 1-3: sink rate, site selection, exchange of rest populations. */
   long long sites = 0;
   double removed = 0.0, min_margin = INFINITY;
+#pragma omp parallel for schedule(static) reduction(+ : sites, removed) reduction(min : min_margin)
   for (long long X = 0; X < N; X++) {
     if (is_solid(p, X)) {
       mask_out[X] = 0;
@@ -463,6 +466,7 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out, const doubl
   }
 
   /* Step 4: moments of every cell, needed by the gradient stencil. */
+#pragma omp parallel for schedule(static)
   for (long long X = 0; X < N; X++) {
     if (is_solid(p, X)) {
       rn[X] = 0.0;
@@ -477,6 +481,7 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out, const doubl
   }
 
   /* Step 5: colour gradient, collision, perturbation, recoloring. */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < p->nz; z++)
     for (int y = 0; y < p->ny; y++)
       for (int x = 0; x < p->nx; x++) {

@@ -16,8 +16,9 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libcgevap.so")
 
-F64, F32, F16DEV, BF16DEV, F32RC = 0, 1, 2, 3, 4
-STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV, "f32rc": F32RC}
+F64, F32, F16DEV, BF16DEV, F32RC, F16RC, BF16RC = 0, 1, 2, 3, 4, 5, 6
+STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV, "f32rc": F32RC,
+           "f16rc": F16RC, "bf16rc": BF16RC}
 DTYPE_F64, DTYPE_F32 = 0, 1
 SITES_GRADIENT, SITES_BAND, SITES_GIVEN = 0, 1, 2
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NAN", -6: "UNSUPPORTED", -7: "IO"}
@@ -104,6 +105,10 @@ _SIGS = {
     "cgevap_ensemble_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cgevap_ensemble_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "cgevap_ensemble_set_active": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "cgevap_ensemble_set_barrier_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cgevap_ensemble_debug_skip_arrival": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "cgevap_ensemble_grid": (ctypes.c_int, [_vp]),
 }
 
 
@@ -373,15 +378,17 @@ def all_signatures():
 
 
 class Ensemble:
-    """Independent lattices advanced together by one persistent launch (FP32 storage)."""
+    """Independent lattices advanced together by one persistent launch; storage "f32" or "f64",
+    one for all members or a list with one per member."""
 
-    def __init__(self, cases):
+    def __init__(self, cases, storage="f32"):
         arr = (Params * len(cases))()
+        st = [storage] * len(cases) if isinstance(storage, str) else list(storage)
         for j, c in enumerate(cases):
             nz, ny, nx = c.shape
             arr[j] = Params(c.q, nx, ny, nz, (ctypes.c_int * 3)(*c.periodic), c.rho_r_in,
                             c.rho_b_in, c.tau_r, c.tau_b, c.sigma, c.beta, c.site_rule,
-                            c.threshold, c.sbar, F32)
+                            c.threshold, c.sbar, STORAGE[st[j]])
         h = _vp()
         rc = lib().cgevap_ensemble_create(arr, len(cases), ctypes.byref(h))
         if rc != 0:
@@ -423,6 +430,19 @@ class Ensemble:
 
     def set_tuning(self, groups: int, planes_3d: int, planes_2d: int):
         self._check(lib().cgevap_ensemble_set_tuning(self._h, groups, planes_3d, planes_2d))
+
+    def set_active(self, j: int, active: bool):
+        self._check(lib().cgevap_ensemble_set_active(self._h, int(j), 1 if active else 0))
+
+    def set_barrier_timeout(self, ms: int):
+        self._check(lib().cgevap_ensemble_set_barrier_timeout(self._h, int(ms)))
+
+    def debug_skip_arrival(self, cta: int, step: int = 0):
+        self._check(lib().cgevap_ensemble_debug_skip_arrival(self._h, int(cta), int(step)))
+
+    @property
+    def grid(self) -> int:
+        return lib().cgevap_ensemble_grid(self._h)
 
     def autotune(self, probe_steps: int = 4) -> float:
         self._sync_stream()

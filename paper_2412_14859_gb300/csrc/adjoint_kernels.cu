@@ -95,6 +95,10 @@ cudaError_t launch_volume(const AuxArgs& a, const void* state, double* part, uns
     case 193: CG_VOL(19, ST_BF16); break;
     case 94: CG_VOL(9, ST_RC); break;
     case 194: CG_VOL(19, ST_RC); break;
+    case 96: CG_VOL(9, ST_H16RC); break;
+    case 97: CG_VOL(9, ST_B16RC); break;
+    case 196: CG_VOL(19, ST_H16RC); break;
+    case 197: CG_VOL(19, ST_B16RC); break;
     default: return cudaErrorInvalidValue;
   }
 #undef CG_VOL

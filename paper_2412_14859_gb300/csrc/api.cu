@@ -48,7 +48,7 @@ std::string validate(const cgevap_params* p) {
   if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND &&
       p->site_rule != CGEVAP_SITES_GIVEN)
     return "unknown site rule";
-  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_F32RC) return "unknown storage";
+  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16RC) return "unknown storage";
   return "";
 }
 
@@ -85,7 +85,7 @@ void setup_physics(cgevap_sim* s) {
     fill_kappa<19>(ph);
   else
     fill_kappa<9>(ph);
-  if (p.storage == CGEVAP_F16DEV) {
+  if (p.storage == CGEVAP_F16DEV || p.storage == CGEVAP_F16RC) {
     const double rmax = std::fmax(p.rho_r_in, p.rho_b_in);
     int e = (int)std::floor(std::log2(16384.0 / rmax));
     if (e > 10) e = 10;
@@ -99,14 +99,31 @@ void setup_physics(cgevap_sim* s) {
 
 }  // namespace
 
+int cgevap::internal_storage(int api_storage) {
+  switch (api_storage) {
+    case CGEVAP_F64: return ST_F64;
+    case CGEVAP_F32: return ST_F32;
+    case CGEVAP_F16DEV: return ST_F16;
+    case CGEVAP_BF16DEV: return ST_BF16;
+    case CGEVAP_F32RC: return ST_RC;
+    case CGEVAP_F16RC: return ST_H16RC;
+    case CGEVAP_BF16RC: return ST_B16RC;
+    default: return -1;
+  }
+}
+
+bool cgevap::is_recolour_on_pull(int api_storage) {
+  return api_storage == CGEVAP_F32RC || api_storage == CGEVAP_F16RC || api_storage == CGEVAP_BF16RC;
+}
+
 AuxArgs cgevap::aux_of(const cgevap_sim* s) {
   AuxArgs a;
   a.g = s->geom;
   a.ph = s->ph;
   mirror_floats(a.ph);
   a.q = s->p.q;
-  // the recolour-on-pull layout holds an imported state as FP32 pairs until the next step
-  a.storage = s->p.storage == CGEVAP_F32RC ? (s->rc_pairs ? ST_F32 : ST_RC) : s->p.storage;
+  // the recolour-on-pull layouts hold an imported state as FP32 pairs until the next step
+  a.storage = is_recolour_on_pull(s->p.storage) && s->rc_pairs ? ST_F32 : internal_storage(s->p.storage);
   a.rho_r_in = s->p.rho_r_in;
   a.rho_b_in = s->p.rho_b_in;
   return a;
@@ -117,16 +134,20 @@ namespace {
 // Arguments of the kernels that write a whole imported state: the recolour-on-pull layout takes
 // it as FP32 pairs (read by the next step's pairs-in kernel).
 AuxArgs import_args(cgevap_sim* s) {
-  if (s->p.storage == CGEVAP_F32RC) s->rc_pairs = 1;
+  if (is_recolour_on_pull(s->p.storage)) s->rc_pairs = 1;
   return aux_of(s);
 }
 
-KernelRef kernel_for(int q, int storage, int variant) {
+// Step kernel of an API storage code; pairs_in: the recolour-on-pull layouts' first step after an
+// import, reading FP32 pairs.
+KernelRef kernel_for(int q, int storage, int variant, bool pairs_in = false) {
   switch (storage) {
     case CGEVAP_F64: return step_kernel_f64(q, variant);
     case CGEVAP_F32: return step_kernel_f32(q, variant);
-    case CGEVAP_F32RC: return step_kernel_rc(q, variant, false);
-    default: return step_kernel_dev(q, storage, variant);
+    case CGEVAP_F32RC: return step_kernel_rc(q, variant, pairs_in);
+    case CGEVAP_F16RC:
+    case CGEVAP_BF16RC: return step_kernel_rc16(q, internal_storage(storage), variant, pairs_in);
+    default: return step_kernel_dev(q, internal_storage(storage), variant);
   }
 }
 
@@ -143,8 +164,8 @@ int plan_launch(cgevap_sim* s, int family, int variant, int pc_force = 0) {
                             : kernel_for(s->p.q, s->p.storage, variant);
   if (!k.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
   KernelRef k_in{nullptr, 0};
-  if (s->p.storage == CGEVAP_F32RC) {  // same tiles, FP32 pairs in
-    k_in = step_kernel_rc(s->p.q, variant, true);
+  if (is_recolour_on_pull(s->p.storage)) {  // same tiles, FP32 pairs in
+    k_in = kernel_for(s->p.q, s->p.storage, variant, true);
     if (!k_in.fn) return fail(s, CGEVAP_ERR_UNSUPPORTED, "no step kernel for this configuration");
   }
   TileCfg t = tile_cfg(s->p.q, variant);
@@ -357,7 +378,7 @@ int cgevap_create(const cgevap_params* p, cgevap_sim** out) {
   g.img_a = 0;  // ghost images are kept only while the TMA kernel is selected
   g.img_b = 0;
   setup_physics(s);
-  s->state_bytes = state_bytes(p->storage, p->q, sh.nstore);
+  s->state_bytes = state_bytes(internal_storage(p->storage), p->q, sh.nstore);
   bool ok = true;
   for (int h = 0; h < 2 && ok; ++h) {
     ok = cudaMalloc(&s->state[h], s->state_bytes) == cudaSuccess &&
@@ -500,8 +521,9 @@ int cgevap_set_flux_heated(cgevap_sim* s, double phi_s, double K, double length,
 
 int cgevap_set_outlets(cgevap_sim* s, double rho_lo, double rho_hi) {
   if (!s) return CGEVAP_ERR_ARG;
-  if (s->p.storage == CGEVAP_F32RC && (rho_lo > 0.0 || rho_hi > 0.0))
-    return fail(s, CGEVAP_ERR_UNSUPPORTED, "outlets need a storage that holds each colour (not F32RC)");
+  if (is_recolour_on_pull(s->p.storage) && (rho_lo > 0.0 || rho_hi > 0.0))
+    return fail(s, CGEVAP_ERR_UNSUPPORTED,
+                "outlets need a storage that holds each colour (not a recolour-on-pull layout)");
   if (!std::isfinite(rho_lo) || !std::isfinite(rho_hi))
     return fail(s, CGEVAP_ERR_ARG, "outlet densities must be finite");
   const bool lo = rho_lo > 0.0, hi = rho_hi > 0.0;
@@ -790,6 +812,8 @@ double cgevap_bytes_per_update(const cgevap_sim* s) {
     case CGEVAP_F64: pops = 2.0 * 2 * Q * 8; break;
     case CGEVAP_F32: pops = 2.0 * 2 * Q * 4; break;
     case CGEVAP_F32RC: pops = 2.0 * (Q * 4 + 16); break;
+    case CGEVAP_F16RC:
+    case CGEVAP_BF16RC: pops = 2.0 * (8 + 16 + 4 + (Q - 1) * 2); break;  // rest pair, record, Rf, deviations
     default: pops = 2.0 * (8 + (Q - 1) * 4); break;
   }
   const double mask = s->p.site_rule == CGEVAP_SITES_BAND ? 1.0 : 2.0;  // read + write

@@ -447,6 +447,10 @@ __global__ void k_fill(double* out, double v, long long n) {
       case 193: KERNEL<19, ST_BF16><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;           \
       case 94: KERNEL<9, ST_RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;               \
       case 194: KERNEL<19, ST_RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;             \
+      case 96: KERNEL<9, ST_H16RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
+      case 97: KERNEL<9, ST_B16RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;            \
+      case 196: KERNEL<19, ST_H16RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;          \
+      case 197: KERNEL<19, ST_B16RC><<<GRID, kThreads, 0, STREAM>>>(__VA_ARGS__); break;          \
       default: return cudaErrorInvalidValue;                                                      \
     }                                                                                             \
   } while (0)
@@ -538,7 +542,8 @@ cudaError_t launch_convert_field(const void* in, int in_dtype, void* out, int ou
 }
 
 cudaError_t launch_outlets(const AuxArgs& a, void* state, double rho_lo, double rho_hi, cudaStream_t s) {
-  if (a.storage == ST_RC) return cudaErrorInvalidValue;  // a colour-blind layout holds no blue half
+  // a colour-blind layout holds no blue half
+  if (a.storage == ST_RC || a.storage == ST_H16RC || a.storage == ST_B16RC) return cudaErrorInvalidValue;
   CGEVAP_DISPATCH(a, k_outlet, grid_for(2LL * a.g.na * a.g.nb), s, a.g, a.ph, state, rho_lo, rho_hi);
   return cudaGetLastError();
 }

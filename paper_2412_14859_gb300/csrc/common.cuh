@@ -190,6 +190,105 @@ struct RcIO {
   }
 };
 
+// c_i . V of a record (w_r, V) for direction i, summed in the order a, b, m: every reader and
+// writer of a recolour-on-pull layout forms it with this function, so the colour split of a
+// population is the same bits wherever it is computed (c_opp(i) . V is exactly -(c_i . V)).
+template <class L>
+__device__ __forceinline__ float rc_cv(int i, const float4& r) {
+  float cv = 0.0f;
+  if (L::ca(i) > 0) cv += r.y;
+  if (L::ca(i) < 0) cv -= r.y;
+  if (L::cb(i) > 0) cv += r.z;
+  if (L::cb(i) < 0) cv -= r.z;
+  if (L::cm(i) > 0) cv += r.w;
+  if (L::cm(i) < 0) cv -= r.w;
+  return cv;
+}
+
+// Red part of a colour-blind population f of direction i whose source record is r; cv is
+// rc_cv(i, r), negated for a bounced link (whose stored direction is opp(i)).
+template <class L>
+__device__ __forceinline__ float rc_red(int i, float w, float f, float cv) {
+  return fmaf(w, f, float(rc_factor<L>(i)) * cv);
+}
+
+// 16-bit recolour-on-pull layout, one cell at a time (auxiliary kernels).  load() decodes and
+// splits as the step's pull does; store() writes exactly only what this layout holds with V = 0
+// and deviations measured from Rf = 0 (used to zero solid cells); other states are imported as
+// FP32 pairs.
+template <int S, int Q>
+struct Rc16IO {
+  using L = Lattice<Q>;
+  using H = typename Storage<S>::half_t;
+  using P = typename H::packed;
+  static __device__ __forceinline__ V2<float> load(const void* base, int nstore, int i, int dir,
+                                                   int si, const Physics& ph) {
+    const char* b = reinterpret_cast<const char*>(base);
+    if (i == 0) {
+      const float2 r0 = __ldg(reinterpret_cast<const float2*>(b) + si);
+      return {r0.x, r0.y};
+    }
+    const Rc16Layout l = rc16_layout(Q, nstore);
+    const float4 rec = __ldg(reinterpret_cast<const float4*>(b + l.rec) + si);
+    const float rf = __ldg(reinterpret_cast<const float*>(b + l.ref) + si);
+    const P d = reinterpret_cast<const P*>(b + l.dev)[(size_t)(dir - 1) * nstore + si];
+    const float f = fmaf(H::unpack(d), ph.inv_scale, float(rc16_ratio<L>(i)) * rf);
+    float cv = rc_cv<L>(i, rec);
+    if (dir != i) cv = -cv;
+    const float fr = rc_red<L>(i, rec.x, f, cv);
+    return {fr, f - fr};
+  }
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, float r, float b) {
+    char* p = reinterpret_cast<char*>(base);
+    const Rc16Layout l = rc16_layout(Q, nstore);
+    if (i == 0) {
+      const float f = r + b;
+      reinterpret_cast<float2*>(p)[si] = make_float2(r, b);
+      reinterpret_cast<float4*>(p + l.rec)[si] = make_float4(f > 0.0f ? r / f : 0.0f, 0.0f, 0.0f, 0.0f);
+      reinterpret_cast<float*>(p + l.ref)[si] = 0.0f;
+      return;
+    }
+    reinterpret_cast<P*>(p + l.dev)[(size_t)(i - 1) * nstore + si] = H::pack(r + b);
+  }
+};
+
+template <int Q>
+struct PopIO<ST_H16RC, Q, false> {
+  using R = float;
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int i, int dir, int si,
+                                               const Physics& ph) {
+    return Rc16IO<ST_H16RC, Q>::load(base, nstore, i, dir, si, ph);
+  }
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
+                                               V2<R>, const Physics&) {
+    Rc16IO<ST_H16RC, Q>::store(base, nstore, i, si, r, b);
+  }
+};
+template <int Q>
+struct PopIO<ST_B16RC, Q, false> {
+  using R = float;
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int i, int dir, int si,
+                                               const Physics& ph) {
+    return Rc16IO<ST_B16RC, Q>::load(base, nstore, i, dir, si, ph);
+  }
+  static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
+                                               V2<R>, const Physics&) {
+    Rc16IO<ST_B16RC, Q>::store(base, nstore, i, si, r, b);
+  }
+};
+// Pairs in (an imported state), 16-bit recolour-on-pull out: the loads of ST_RCI.
+template <int Q>
+struct PopIO<ST_H16RCI, Q, false> {
+  using R = float;
+  static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int, int dir, int si,
+                                               const Physics&) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(base) + (size_t)dir * nstore + si);
+    return {v.x, v.y};
+  }
+};
+template <int Q>
+struct PopIO<ST_B16RCI, Q, false> : PopIO<ST_H16RCI, Q, false> {};
+
 template <int Q>
 struct PopIO<ST_RC, Q, false> {
   using R = float;

@@ -6,11 +6,13 @@
 // the single-lattice step kernel splits it.  A D3Q19 item fills a 128-thread CTA (32 x 4 tile;
 // four CTAs per SM, as the fastest single-lattice step); D2Q9 items are narrower and run G at a
 // time in one CTA, one per group of 128/G threads (row tiles of 128/G cells), with their barrier
-// rounds padded to the longest chunk of the pack.
-// CTAs take items (or packs) in a strided loop, meet at a grid barrier after every step, and fold
+// rounds padded to the longest chunk of the pack.  Members store FP32 or FP64 populations; a
+// pack holds items of one storage only, so every barrier round of a CTA runs the same code.
+// CTAs take items (or packs) from a counter, meet at a grid barrier after every step, and fold
 // the per-item ledger partials of each member in item order (deterministic).  Every wait is
-// bounded; a barrier that gives up sets the status word, the CTAs finish their loops and the
-// host reports CGEVAP_ERR_TIMEOUT.
+// bounded (4 s by default, settable from the host); a barrier that gives up sets the status
+// word, the CTAs finish their loops and the host reports CGEVAP_ERR_TIMEOUT.  Paused members
+// have no items: their state, site bytes and ledger stay as they are.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,7 +35,8 @@ struct EnsMember {
   uint8_t* mask[2];
   DevLedger* ledger;
   int q;
-  int item0, nitem;     // its items: [item0, item0 + nitem) of the concatenated list
+  int storage;          // ST_F32 or ST_F64
+  int item0, nitem;     // its items: [item0, item0 + nitem) of the concatenated list (0: paused)
 };
 
 struct EnsArgs {
@@ -49,12 +52,16 @@ struct EnsArgs {
   unsigned int* bar;     // [4]: arrivals, generation, work counters of even / odd steps
   int* status;
   int nsteps;
+  unsigned long long barrier_ns;  // limit of one grid-barrier wait
+  int skip_cta, skip_step;        // test hook: this CTA does not arrive after this step (-1: off)
 };
 
-// Grid-wide barrier of a cooperative launch; gives up after ~4 s and sets *status.
-__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status) {
+// Grid-wide barrier of a cooperative launch; a wait gives up after limit_ns and sets *status.
+// skip: this CTA does not arrive (test hook that makes the other CTAs' waits run out).
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status,
+                                             unsigned long long limit_ns, bool skip) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !skip) {
     volatile unsigned int* vgen = bar + 1;
     const unsigned int gen = *vgen;
     __threadfence();
@@ -68,7 +75,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status) {
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
       while (*vgen == gen) {
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 4000000000ull) {
+        if (t - t0 > limit_ns) {
           atomicExch(status, 1);
           break;
         }
@@ -82,8 +89,18 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status) {
 constexpr int kEnsThreads = 128;  // threads per CTA
 constexpr int kEnsTy = 4;         // D3Q19 item tile: 32 x kEnsTy columns
 
-template <int G>
-__global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __grid_constant__ EnsArgs E) {
+// Member storages a kernel instantiation handles: FP32 only, FP64 only, or both.
+enum { kEnsF32 = 0, kEnsF64 = 1, kEnsMixed = 2 };
+
+// Shared memory of one D2Q9 group / one D3Q19 item of storage S.
+template <int G, int S>
+constexpr int ens_group_smem() {
+  return TileSmem<9, S, kEnsThreads / G, 1, 1>::BYTES;
+}
+
+template <int G, int MODE>
+__global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
+    cg_ensemble_kernel(const __grid_constant__ EnsArgs E) {
   constexpr int NT = kEnsThreads;
   constexpr int GT = NT / G;  // threads per D2Q9 group
   extern __shared__ __align__(16) unsigned char smem[];
@@ -118,7 +135,11 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
         A.pout = M.state[c ^ 1];
         A.mask_in = M.mask[c];
         A.mask_out = M.mask[c ^ 1];
-        step_tile<19, ST_F32, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
+        const bool f64 = MODE == kEnsF64 || (MODE == kEnsMixed && M.storage == ST_F64);
+        if (MODE != kEnsF64 && !f64)
+          step_tile<19, ST_F32, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
+        else if (MODE != kEnsF32)
+          step_tile<19, ST_F64, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
         block_sum<NT>(n, d);
         if (tid == 0) {
           pr[w] = d;
@@ -129,7 +150,10 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
         const int4 it = E.items[E.n3 + pack * G + grp];
         int iters = 0;
         for (int g = 0; g < G; ++g) iters = max(iters, E.items[E.n3 + pack * G + g].w);
-        unsigned char* gs = smem + grp * TileSmem<9, ST_F32, GT, 1, 1>::BYTES;
+        // the pack's storage: that of its first item, which is never a filler
+        const bool f64 = MODE == kEnsF64 ||
+                         (MODE == kEnsMixed && E.members[E.items[E.n3 + pack * G].x].storage == ST_F64);
+        unsigned char* gs = smem + grp * (f64 ? ens_group_smem<G, ST_F64>() : ens_group_smem<G, ST_F32>());
         if (it.x >= 0) {
           const EnsMember& M = E.members[it.x];
           StepArgs A = M.a;
@@ -138,7 +162,10 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
           A.pout = M.state[c ^ 1];
           A.mask_in = M.mask[c];
           A.mask_out = M.mask[c ^ 1];
-          step_tile<9, ST_F32, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
+          if (MODE != kEnsF64 && !f64)
+            step_tile<9, ST_F32, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
+          else if (MODE != kEnsF32)
+            step_tile<9, ST_F64, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
         } else {
           for (int r = 0; r < 1 + iters; ++r) __syncthreads();  // same barrier rounds, no work
         }
@@ -166,7 +193,8 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
         __syncthreads();
       }
     }
-    grid_barrier(E.bar, E.status);
+    grid_barrier(E.bar, E.status, E.barrier_ns,
+                 (int)blockIdx.x == E.skip_cta && step == E.skip_step);
     // this step's counter is next used two steps on, after one more barrier
     if (blockIdx.x == 0 && tid == 0) E.bar[2 + par] = 0u;
     // a barrier that gave up ends the launch in every CTA (each waits at most once more)
@@ -178,6 +206,7 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
     if (tid == 0) {
       for (int j = blockIdx.x; j < E.nmembers; j += gridDim.x) {
         const EnsMember& M = E.members[j];
+        if (M.nitem == 0) continue;  // paused: its ledger does not move
         double s = 0.0;
         long long k = 0;
         for (int i = 0; i < M.nitem; ++i) {  // the member's items, through the index table
@@ -196,17 +225,21 @@ __global__ void __launch_bounds__(kEnsThreads, 4) cg_ensemble_kernel(const __gri
   }
 }
 
-// Resident CTAs of the ensemble kernel for group count G (0 on error), and its launcher.
-template <int G>
+// Dynamic shared memory of the ensemble kernel for group count G and member storages MODE.
+template <int G, int MODE>
 static int ens_smem() {
-  constexpr int b2 = G * TileSmem<9, ST_F32, kEnsThreads / G, 1, 1>::BYTES;
-  constexpr int b3 = TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES;
-  return b2 > b3 ? b2 : b3;
+  constexpr int b32 = G * ens_group_smem<G, ST_F32>() > TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES
+                          ? G * ens_group_smem<G, ST_F32>()
+                          : TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES;
+  constexpr int b64 = G * ens_group_smem<G, ST_F64>() > TileSmem<19, ST_F64, 32, kEnsTy, 1>::BYTES
+                          ? G * ens_group_smem<G, ST_F64>()
+                          : TileSmem<19, ST_F64, 32, kEnsTy, 1>::BYTES;
+  return MODE == kEnsF32 ? b32 : (MODE == kEnsF64 ? b64 : (b32 > b64 ? b32 : b64));
 }
 
-template <int G>
+template <int G, int MODE>
 static const void* ens_fn() {
-  return (const void*)cg_ensemble_kernel<G>;
+  return (const void*)cg_ensemble_kernel<G, MODE>;
 }
 
 }  // namespace cgevap
@@ -230,6 +263,10 @@ struct cgevap_ens {
   unsigned int* d_bar = nullptr;
   int* d_status = nullptr;
   size_t items_cap = 0;
+  int mode = kEnsF32;                  // member storages (kEnsF32 / kEnsF64 / kEnsMixed)
+  std::vector<int> active;             // 0: member paused (no items)
+  unsigned long long barrier_ns = 4000000000ull;
+  int skip_cta = -1, skip_step = -1;   // test hook of the grid barrier
   // plan
   int groups = 4;        // D2Q9 items per CTA
   int pc3 = 16, pc2 = 32;
@@ -258,18 +295,35 @@ int efail(cgevap_ens* e, int code, const std::string& m) {
       return efail((e), CGEVAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(r_)); \
   } while (0)
 
-const void* kernel_for_groups(int g) {
-  switch (g) {
-    case 2: return ens_fn<2>();
-    case 4: return ens_fn<4>();
+const void* kernel_for_groups(int g, int mode) {
+  switch (g * 4 + mode) {
+    case 2 * 4 + kEnsF32: return ens_fn<2, kEnsF32>();
+    case 4 * 4 + kEnsF32: return ens_fn<4, kEnsF32>();
+    case 2 * 4 + kEnsF64: return ens_fn<2, kEnsF64>();
+    case 4 * 4 + kEnsF64: return ens_fn<4, kEnsF64>();
+    case 2 * 4 + kEnsMixed: return ens_fn<2, kEnsMixed>();
+    case 4 * 4 + kEnsMixed: return ens_fn<4, kEnsMixed>();
     default: return nullptr;
   }
 }
-int smem_for_groups(int g) {
-  switch (g) {
-    case 2: return ens_smem<2>();
-    case 4: return ens_smem<4>();
+int smem_for_groups(int g, int mode) {
+  switch (g * 4 + mode) {
+    case 2 * 4 + kEnsF32: return ens_smem<2, kEnsF32>();
+    case 4 * 4 + kEnsF32: return ens_smem<4, kEnsF32>();
+    case 2 * 4 + kEnsF64: return ens_smem<2, kEnsF64>();
+    case 4 * 4 + kEnsF64: return ens_smem<4, kEnsF64>();
+    case 2 * 4 + kEnsMixed: return ens_smem<2, kEnsMixed>();
+    case 4 * 4 + kEnsMixed: return ens_smem<4, kEnsMixed>();
     default: return 0;
+  }
+}
+
+// The cached graph holds the launch's arguments: drop it when they change.
+void drop_graph(cgevap_ens* e) {
+  if (e->graph) {
+    cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
+    e->graph_steps = -1;
   }
 }
 
@@ -285,6 +339,7 @@ int build_plan(cgevap_ens* e) {
     EnsMember& M = mem[j];
     std::memset(&M, 0, sizeof(M));
     M.q = e->params[j].q;
+    M.storage = e->params[j].storage == CGEVAP_F64 ? ST_F64 : ST_F32;
     M.a.g = v.g;
     M.a.ph = v.ph;
     M.state[0] = v.state[0];
@@ -298,6 +353,7 @@ int build_plan(cgevap_ens* e) {
     M.a.nty = (v.g.nb + ty - 1) / ty;
     M.a.pc = std::min(pc, v.g.nm);
     const int nch = (v.g.nm + M.a.pc - 1) / M.a.pc;
+    if (!e->active[j]) continue;  // paused: no items
     for (int t = 0; t < M.a.ntx * M.a.nty; ++t)
       for (int c = 0; c < nch; ++c) {
         const int planes = std::min(M.a.pc, v.g.nm - c * M.a.pc);
@@ -314,11 +370,19 @@ int build_plan(cgevap_ens* e) {
   for (int j : order)
     for (const int4& v : per3[j]) items.push_back(v);
   const int n3 = (int)items.size();
+  // D2Q9 items: FP32 members' packs, then FP64 members' packs (one storage per pack), each
+  // padded with fillers (member -1) to whole packs
   std::vector<int4> flat2;
-  for (int j : order)
-    for (const int4& v : per2[j]) flat2.push_back(v);
-  std::stable_sort(flat2.begin(), flat2.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
-  while (flat2.size() % e->groups) flat2.push_back(make_int4(-1, 0, 0, 0));
+  for (int st : {ST_F32, ST_F64}) {
+    std::vector<int4> part;
+    for (int j : order)
+      if (mem[j].storage == st)
+        for (const int4& v : per2[j]) part.push_back(v);
+    std::stable_sort(part.begin(), part.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+    if (part.empty()) continue;
+    while (part.size() % e->groups) part.push_back(make_int4(-1, 0, 0, 0));
+    flat2.insert(flat2.end(), part.begin(), part.end());
+  }
   for (const int4& v : flat2) items.push_back(v);
   // member -> its items (contiguous ranges are not guaranteed: record by scanning)
   // Partials are indexed by item; a member's fold walks a per-member index list stored after
@@ -363,19 +427,15 @@ int build_plan(cgevap_ens* e) {
   EN_CUDA(e, cudaMemcpyAsync(e->d_members, e->h_members.data(), e->n * sizeof(EnsMember),
                              cudaMemcpyHostToDevice, e->stream));
   // resident CTAs
-  const void* fn = kernel_for_groups(e->groups);
-  e->smem = smem_for_groups(e->groups);
+  const void* fn = kernel_for_groups(e->groups, e->mode);
+  e->smem = smem_for_groups(e->groups, e->mode);
   EN_CUDA(e, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem));
   int occ = 0, sms = 0;
   EN_CUDA(e, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kEnsThreads, e->smem));
   EN_CUDA(e, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
   if (occ < 1) return efail(e, CGEVAP_ERR_UNSUPPORTED, "ensemble kernel does not fit on an SM");
   e->grid = std::min(occ * sms, std::max(1, e->n3 + e->npack));
-  if (e->graph) {
-    cudaGraphExecDestroy(e->graph);
-    e->graph = nullptr;
-    e->graph_steps = -1;
-  }
+  drop_graph(e);
   return CGEVAP_OK;
 }
 
@@ -394,6 +454,9 @@ int launch(cgevap_ens* e, int nsteps) {
   a.bar = e->d_bar;
   a.status = e->d_status;
   a.nsteps = nsteps;
+  a.barrier_ns = e->barrier_ns;
+  a.skip_cta = e->skip_cta;
+  a.skip_step = e->skip_step;
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(e->grid);
@@ -406,14 +469,16 @@ int launch(cgevap_ens* e, int nsteps) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {&a};
-  // the work counters start at zero (a launch whose barrier gave up may have left them set)
-  EN_CUDA(e, cudaMemsetAsync(e->d_bar + 2, 0, 2 * sizeof(unsigned int), e->stream));
-  EN_CUDA(e, cudaLaunchKernelExC(&cfg, kernel_for_groups(e->groups), args));
+  // arrivals, generation and work counters start at zero (a launch whose barrier gave up may
+  // have left arrivals counted and counters set)
+  EN_CUDA(e, cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned int), e->stream));
+  EN_CUDA(e, cudaLaunchKernelExC(&cfg, kernel_for_groups(e->groups, e->mode), args));
   return CGEVAP_OK;
 }
 
 void sync_member_cur(cgevap_ens* e, int nsteps) {
   for (int j = 0; j < e->n; ++j) {
+    if (!e->active[j]) continue;
     e->cur[j] ^= (nsteps & 1);
     SimView v;
     sim_view(e->sims[j], &v);
@@ -432,11 +497,17 @@ int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out
   if (!e) return CGEVAP_ERR_OOM;
   e->n = n;
   cudaGetDevice(&e->device);
+  int seen = 0;  // bit 0: an FP32 member, bit 1: an FP64 member
   for (int j = 0; j < n; ++j) {
-    if (members[j].storage != CGEVAP_F32) {
+    if (members[j].storage != CGEVAP_F32 && members[j].storage != CGEVAP_F64) {
       cgevap_ensemble_destroy(e);
       return CGEVAP_ERR_UNSUPPORTED;
     }
+    seen |= members[j].storage == CGEVAP_F64 ? 2 : 1;
+  }
+  e->mode = seen == 1 ? kEnsF32 : (seen == 2 ? kEnsF64 : kEnsMixed);
+  e->active.assign(n, 1);
+  for (int j = 0; j < n; ++j) {
     cgevap_sim* s = nullptr;
     int rc = cgevap_create(&members[j], &s);
     if (rc != CGEVAP_OK) {
@@ -446,7 +517,6 @@ int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out
     e->sims.push_back(s);
     e->params.push_back(members[j]);
     e->cur.push_back(0);
-    e->cells += (long long)members[j].nx * members[j].ny * members[j].nz;
   }
   if (cudaMalloc(&e->d_members, n * sizeof(EnsMember)) != cudaSuccess ||
       cudaMalloc(&e->d_cur, n * sizeof(int)) != cudaSuccess ||
@@ -485,7 +555,41 @@ const char* cgevap_ensemble_last_error(const cgevap_ens* e) { return e ? e->err.
 
 int cgevap_ensemble_size(const cgevap_ens* e) { return e ? e->n : 0; }
 
-long long cgevap_ensemble_cells(const cgevap_ens* e) { return e ? e->cells : 0; }
+long long cgevap_ensemble_cells(const cgevap_ens* e) {
+  if (!e) return 0;
+  long long c = 0;
+  for (int j = 0; j < e->n; ++j)
+    if (e->active[j]) c += (long long)e->params[j].nx * e->params[j].ny * e->params[j].nz;
+  return c;
+}
+
+int cgevap_ensemble_set_active(cgevap_ens* e, int j, int active) {
+  if (!e || j < 0 || j >= e->n || (active != 0 && active != 1)) return CGEVAP_ERR_ARG;
+  if (e->active[j] == active) return CGEVAP_OK;
+  int any = 0;
+  for (int k = 0; k < e->n; ++k) any |= k == j ? active : e->active[k];
+  if (!any) return efail(e, CGEVAP_ERR_ARG, "an ensemble needs at least one active member");
+  EN_CUDA(e, cudaSetDevice(e->device));
+  e->active[j] = active;
+  return build_plan(e);
+}
+
+int cgevap_ensemble_set_barrier_timeout(cgevap_ens* e, int ms) {
+  if (!e || ms < 1) return CGEVAP_ERR_ARG;
+  e->barrier_ns = (unsigned long long)ms * 1000000ull;
+  drop_graph(e);
+  return CGEVAP_OK;
+}
+
+int cgevap_ensemble_debug_skip_arrival(cgevap_ens* e, int cta, int step) {
+  if (!e || cta < -1 || (cta >= 0 && step < 0)) return CGEVAP_ERR_ARG;
+  e->skip_cta = cta;
+  e->skip_step = cta < 0 ? -1 : step;
+  drop_graph(e);
+  return CGEVAP_OK;
+}
+
+int cgevap_ensemble_grid(const cgevap_ens* e) { return e ? e->grid : 0; }
 
 int cgevap_ensemble_member(cgevap_ens* e, int j, cgevap_sim** out) {
   if (!e || !out || j < 0 || j >= e->n) return CGEVAP_ERR_ARG;
@@ -497,11 +601,7 @@ int cgevap_ensemble_set_stream(cgevap_ens* e, void* stream) {
   if (!e) return CGEVAP_ERR_ARG;
   e->stream = (cudaStream_t)stream;
   for (cgevap_sim* s : e->sims) cgevap_set_stream(s, stream);
-  if (e->graph) {
-    cudaGraphExecDestroy(e->graph);
-    e->graph = nullptr;
-    e->graph_steps = -1;
-  }
+  drop_graph(e);
   return CGEVAP_OK;
 }
 

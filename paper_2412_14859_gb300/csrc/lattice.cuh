@@ -127,48 +127,61 @@ __host__ __device__ constexpr uint32_t dirs_where(int axis, int sign) {
 //   floats per cell instead of 2Q.  Arbitrary population pairs (an initial state with noise,
 //   an import) are not of this form: those are held as FP32 pairs and the first step reads them
 //   with ST_RCI (pairs in, ST_RC out).
-enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_RC = 4, ST_RCI = 5 };
+// ST_H16RC / ST_B16RC ("recolour on pull, 16-bit"): the colour-blind populations of ST_RC held as
+//   FP16 / BF16 deviations from the lattice-weight rest state of the cell, with each colour's
+//   mass carried exactly.  Per cell, in four arrays (offsets in Rc16Layout):
+//     float2 rest[cell] = (f_0^r, f_0^b)        the rest populations of both colours (FP32),
+//     float4 rec[cell]  = (w_r, V)              as ST_RC,
+//     float  ref[cell]  = Rf                    the rest-state scale, Rf = A_1 rho (1 - abar),
+//     P      dev[i-1][cell] = s (f_i - r_i Rf)  i >= 1, FP16 / BF16, r_i = A_i / A_1,
+//   so f_i^eq(rho, 0) = rho phi_i(abar) = r_i Rf and a cell at rest stores deviations near 0.  A
+//   reader decodes f_i = fl(r_i Rf + dev / s) (r_i is 1 or a power of two: one rounding) and
+//   splits it as ST_RC does: f_i^r = fl(w_r f_i + s_|c| (c_i . V)), f_i^b = fl(f_i - f_i^r).  The
+//   writer forms those same values and sets the rest pair to the exact colour masses minus what
+//   the moving populations will deliver, so the mass of each colour a cell stores is its exact
+//   post-exchange mass up to the rounding of the rest pair.  ST_H16RCI / ST_B16RCI: the same
+//   step reading FP32 pairs (an imported state).
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_RC = 4, ST_RCI = 5, ST_H16RC = 6,
+       ST_B16RC = 7, ST_H16RCI = 8, ST_B16RCI = 9 };
 
+// Traits of a storage code: dev = per-colour 16-bit deviations; rc = writes a recolour-on-pull
+// layout; rc16 = that layout is the 16-bit one; rc_in = reads a recolour-on-pull layout (the
+// pulls need the sources' records, staged in shared memory).
 template <int S>
 struct Storage;
 template <>
 struct Storage<ST_F64> {
   using real = double;
   using vec = double2;
-  static constexpr bool dev = false;
-  static constexpr bool rc = false;
+  static constexpr bool dev = false, rc = false, rc16 = false, rc_in = false;
   static constexpr int bytes_per_pop = 8;
 };
 template <>
 struct Storage<ST_F32> {
   using real = float;
   using vec = float2;
-  static constexpr bool dev = false;
-  static constexpr bool rc = false;
+  static constexpr bool dev = false, rc = false, rc16 = false, rc_in = false;
   static constexpr int bytes_per_pop = 4;
 };
 template <>
 struct Storage<ST_RC> {  // reads and writes the recolour-on-pull layout
   using real = float;
   using vec = float2;
-  static constexpr bool dev = false;
-  static constexpr bool rc = true;
+  static constexpr bool dev = false, rc = true, rc16 = false, rc_in = true;
   static constexpr int bytes_per_pop = 4;
 };
 template <>
 struct Storage<ST_RCI> {  // reads FP32 pairs, writes the recolour-on-pull layout
   using real = float;
   using vec = float2;
-  static constexpr bool dev = false;
-  static constexpr bool rc = true;
+  static constexpr bool dev = false, rc = true, rc16 = false, rc_in = false;
   static constexpr int bytes_per_pop = 4;
 };
 template <>
 struct Storage<ST_F16> {
   using real = float;
   using packed = __half2;
-  static constexpr bool dev = true;
-  static constexpr bool rc = false;
+  static constexpr bool dev = true, rc = false, rc16 = false, rc_in = false;
   static constexpr int bytes_per_pop = 2;
   static __device__ __forceinline__ float2 unpack(packed p) { return __half22float2(p); }
   static __device__ __forceinline__ packed pack(float r, float b) { return __floats2half2_rn(r, b); }
@@ -177,14 +190,40 @@ template <>
 struct Storage<ST_BF16> {
   using real = float;
   using packed = __nv_bfloat162;
-  static constexpr bool dev = true;
-  static constexpr bool rc = false;
+  static constexpr bool dev = true, rc = false, rc16 = false, rc_in = false;
   static constexpr int bytes_per_pop = 2;
   static __device__ __forceinline__ float2 unpack(packed p) { return __bfloat1622float2(p); }
   static __device__ __forceinline__ packed pack(float r, float b) {
     return __floats2bfloat162_rn(r, b);
   }
 };
+// 16-bit recolour-on-pull: one 16-bit value per moving population
+struct Half16 {
+  using packed = __half;
+  static __device__ __forceinline__ float unpack(packed p) { return __half2float(p); }
+  static __device__ __forceinline__ packed pack(float v) { return __float2half_rn(v); }
+};
+struct BHalf16 {
+  using packed = __nv_bfloat16;
+  static __device__ __forceinline__ float unpack(packed p) { return __bfloat162float(p); }
+  static __device__ __forceinline__ packed pack(float v) { return __float2bfloat16_rn(v); }
+};
+template <class H, bool PAIRS_IN>
+struct Rc16Storage {
+  using real = float;
+  using vec = float2;
+  using half_t = H;
+  static constexpr bool dev = false, rc = true, rc16 = true, rc_in = !PAIRS_IN;
+  static constexpr int bytes_per_pop = 2;
+};
+template <>
+struct Storage<ST_H16RC> : Rc16Storage<Half16, false> {};
+template <>
+struct Storage<ST_B16RC> : Rc16Storage<BHalf16, false> {};
+template <>
+struct Storage<ST_H16RCI> : Rc16Storage<Half16, true> {};
+template <>
+struct Storage<ST_B16RCI> : Rc16Storage<BHalf16, true> {};
 
 // Byte offset of the deviation block inside one state buffer of a deviation storage.
 __host__ __device__ inline size_t dev_block_offset(long long nstore) {
@@ -219,12 +258,42 @@ __host__ __device__ constexpr double rc_factor(int i) {
   return L::speed2(i) == 0 ? 0.0 : L::A(i) * inv_norm<L>(i);
 }
 
+// Byte offsets of the arrays of a 16-bit recolour-on-pull state buffer (each 256-byte aligned):
+// rest pairs at 0, records at rec, rest-state scales at ref, deviations at dev; total bytes.
+struct Rc16Layout {
+  size_t rec, ref, dev, total;
+};
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+__host__ __device__ inline Rc16Layout rc16_layout(int q, long long nstore) {
+  Rc16Layout l;
+  l.rec = align256((size_t)nstore * 8);
+  l.ref = align256(l.rec + (size_t)nstore * 16);
+  l.dev = align256(l.ref + (size_t)nstore * 4);
+  l.total = l.dev + (size_t)(q - 1) * nstore * 2;
+  return l;
+}
+
+// Ratio r_i = A_i / A_1 of the rest state of direction i >= 1 to that of an axis direction:
+// 1 or a power of two (D3Q19 1/2, D2Q9 1/4), so r_i Rf is exact.
+template <class L>
+__host__ __device__ constexpr double rc16_ratio(int i) {
+  return L::A(i) / L::A(1);
+}
+
 __host__ inline size_t state_bytes(int storage, int q, long long nstore) {
   switch (storage) {
     case ST_F64: return (size_t)q * nstore * sizeof(double2);
     case ST_F32:
     case ST_RC:  // room for the FP32 pairs of an imported state
     case ST_RCI: return (size_t)q * nstore * sizeof(float2);
+    case ST_H16RC:
+    case ST_B16RC:
+    case ST_H16RCI:
+    case ST_B16RCI: {  // room for the FP32 pairs of an imported state as well
+      const size_t pairs = (size_t)q * nstore * sizeof(float2);
+      const size_t own = rc16_layout(q, nstore).total;
+      return pairs > own ? pairs : own;
+    }
     default: return dev_block_offset(nstore) + (size_t)(q - 1) * nstore * 4;
   }
 }

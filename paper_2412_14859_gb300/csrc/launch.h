@@ -35,6 +35,8 @@ KernelRef step_kernel_f32(int q, int variant);
 KernelRef step_kernel_dev(int q, int storage, int variant);
 // Recolour-on-pull layout (step_rc.cu); pairs_in: the input state holds FP32 pairs (import).
 KernelRef step_kernel_rc(int q, int variant, bool pairs_in);
+// 16-bit recolour-on-pull layouts (step_rc16.cu); storage is ST_H16RC or ST_B16RC.
+KernelRef step_kernel_rc16(int q, int storage, int variant, bool pairs_in);
 // TMA-pipelined step (step_tma_f32.cu): FP32 storage; periodic axes need >= 4 cells.
 constexpr int kNumTmaVariants3D = 2;
 constexpr int kNumTmaVariants2D = 2;

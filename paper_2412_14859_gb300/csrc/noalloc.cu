@@ -6,13 +6,16 @@
 // JAX program, an application arena with a fixed budget), or code that must not call into the
 // allocator at step time.  They pass the state, site bytes and ledger they own; the only scratch
 // the kernel needs lives in the file-scope array below, sized for kMaxBlocks CTAs.
-#include <atomic>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <mutex>
+#include <string>
 
-#include "../../include/cgevap.h"
-#include "launch.h"
+#include "sim.h"
 
 using namespace cgevap;
 
@@ -36,18 +39,50 @@ static_assert(offsetof(cgevap_ledger, steps) == offsetof(DevLedger, steps), "led
 
 namespace {
 
-std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
+// Per device: the scratch's device address and the CUDA context it was resolved in.  A device
+// reset (cudaDeviceReset) replaces the primary context and with it the address, so the address is
+// resolved again whenever the current context differs from the recorded one.
+struct ScratchAddr {
+  CUcontext ctx = nullptr;
+  unsigned char* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
 
-// Resolve the device address of g_scratch for the current device (once per device).
-int scratch_on(int device, unsigned char** out) {
-  unsigned char* p = g_scratch_addr[device].load(std::memory_order_acquire);
-  if (!p) {
-    void* addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || !addr) return CGEVAP_ERR_CUDA;
-    p = static_cast<unsigned char*>(addr);
-    g_scratch_addr[device].store(p, std::memory_order_release);
+int fail(int code, const std::string& msg) { return cgevap::sim_fail(nullptr, code, msg); }
+
+// The current context (driver API, through the runtime's entry-point query; nullptr on failure).
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+  if (!get) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &qr) !=
+            cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    get = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
   }
-  *out = p;
+  CUcontext c = nullptr;
+  return get(&c) == CUDA_SUCCESS ? c : nullptr;
+}
+
+// Resolve the device address of g_scratch for the current device, once per device and context.
+int scratch_on(int device, unsigned char** out) {
+  const CUcontext ctx = current_context();
+  if (!ctx) return fail(CGEVAP_ERR_CUDA, "static-scratch step: no current CUDA context");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  ScratchAddr& e = g_scratch_addr[device];
+  if (!e.addr || e.ctx != ctx) {
+    void* addr = nullptr;
+    const cudaError_t rc = cudaGetSymbolAddress(&addr, g_scratch);
+    if (rc != cudaSuccess || !addr)
+      return fail(CGEVAP_ERR_CUDA, std::string("static-scratch step: cudaGetSymbolAddress: ") +
+                                       cudaGetErrorString(rc));
+    e.addr = static_cast<unsigned char*>(addr);
+    e.ctx = ctx;
+  }
+  *out = e.addr;
   return CGEVAP_OK;
 }
 
@@ -87,19 +122,26 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
     const cgevap_params* p, double phi, const void* dev_state_in, void* dev_state_out,
     size_t state_bytes_in, const uint8_t* dev_mask_in, uint8_t* dev_mask_out,
     cgevap_ledger* dev_ledger, void* cuda_stream) {
-  if (!params_ok(p) || !std::isfinite(phi)) return CGEVAP_ERR_ARG;
+  if (!params_ok(p) || !std::isfinite(phi))
+    return fail(CGEVAP_ERR_ARG, "static-scratch step: invalid parameters or non-finite phi");
   if (!dev_state_in || !dev_state_out || dev_state_in == dev_state_out || !dev_mask_in ||
       !dev_mask_out || !dev_ledger)
-    return CGEVAP_ERR_ARG;
+    return fail(CGEVAP_ERR_ARG, "static-scratch step: NULL or aliasing buffers");
   const long long N = (long long)p->nx * p->ny * p->nz;
   const StoreShape sh = store_shape(p->q, p->nx, p->ny, p->nz);
-  if ((long long)p->q * sh.nstore >= (1LL << 31)) return CGEVAP_ERR_ARG;
-  if (state_bytes_in != state_bytes(p->storage, p->q, sh.nstore)) return CGEVAP_ERR_ARG;
+  if ((long long)p->q * sh.nstore >= (1LL << 31))
+    return fail(CGEVAP_ERR_ARG, "static-scratch step: lattice too large for 32-bit storage indices");
+  const size_t want = state_bytes(internal_storage(p->storage), p->q, sh.nstore);
+  if (state_bytes_in != want)
+    return fail(CGEVAP_ERR_ARG, "static-scratch step: state_bytes is " + std::to_string(state_bytes_in) +
+                                    ", the layout needs " + std::to_string(want));
   int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return CGEVAP_ERR_CUDA;
-  if (device < 0 || device >= kMaxDevices) return CGEVAP_ERR_UNSUPPORTED;
+  if (cudaGetDevice(&device) != cudaSuccess) return fail(CGEVAP_ERR_CUDA, "static-scratch step: no device");
+  if (device < 0 || device >= kMaxDevices)
+    return fail(CGEVAP_ERR_UNSUPPORTED, "static-scratch step: device ordinal beyond 63");
   unsigned char* scratch = nullptr;
-  if (scratch_on(device, &scratch) != CGEVAP_OK) return CGEVAP_ERR_CUDA;
+  const int src = scratch_on(device, &scratch);
+  if (src != CGEVAP_OK) return src;
 
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -158,12 +200,12 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
 
   KernelRef k = p->storage == CGEVAP_F64   ? step_kernel_f64(p->q, 0)
                 : p->storage == CGEVAP_F32 ? step_kernel_f32(p->q, 0)
-                                           : step_kernel_dev(p->q, p->storage, 0);
-  if (!k.fn) return CGEVAP_ERR_UNSUPPORTED;
+                                           : step_kernel_dev(p->q, internal_storage(p->storage), 0);
+  if (!k.fn) return fail(CGEVAP_ERR_UNSUPPORTED, "static-scratch step: no kernel for this storage");
   int occ = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.threads, k.smem) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-    return CGEVAP_ERR_CUDA;
+    return fail(CGEVAP_ERR_CUDA, "static-scratch step: occupancy query failed");
   if (occ < 1) occ = 1;
   TileCfg t = tile_cfg(p->q, 0);
   if (k.tx > 0) t = TileCfg{k.tx, k.ty};
@@ -184,11 +226,14 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
     }
   }
   const long long nchunk = (g.nm + best_pc - 1) / best_pc;
-  if (tiles * nchunk > kMaxBlocks) return CGEVAP_ERR_ARG;  // lattice too large for the scratch
+  if (tiles * nchunk > kMaxBlocks)  // lattice too large for the scratch
+    return fail(CGEVAP_ERR_ARG, "static-scratch step: the grid needs " + std::to_string(tiles * nchunk) +
+                                    " CTAs, more than the 16384 the static scratch holds");
 
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   unsigned int* done = reinterpret_cast<unsigned int*>(scratch + kDoneOff);
-  if (cudaMemsetAsync(done, 0, sizeof(unsigned int), stream) != cudaSuccess) return CGEVAP_ERR_CUDA;
+  if (cudaMemsetAsync(done, 0, sizeof(unsigned int), stream) != cudaSuccess)
+    return fail(CGEVAP_ERR_CUDA, "static-scratch step: clearing the arrival counter failed");
   a.red.part_removed = reinterpret_cast<double*>(scratch + kRemovedOff);
   a.red.part_sites = reinterpret_cast<long long*>(scratch + kSitesOff);
   a.red.done = done;
@@ -201,8 +246,9 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
   a.mask_in = dev_mask_in;
   a.mask_out = dev_mask_out;
   void* args[] = {&a};
-  if (cudaLaunchKernel(k.fn, dim3((unsigned)tiles, (unsigned)nchunk), dim3(k.threads), args,
-                       k.smem, stream) != cudaSuccess)
-    return CGEVAP_ERR_CUDA;
+  const cudaError_t lrc = cudaLaunchKernel(k.fn, dim3((unsigned)tiles, (unsigned)nchunk),
+                                           dim3(k.threads), args, k.smem, stream);
+  if (lrc != cudaSuccess)
+    return fail(CGEVAP_ERR_CUDA, std::string("static-scratch step: launch: ") + cudaGetErrorString(lrc));
   return CGEVAP_OK;
 }

@@ -65,6 +65,10 @@ namespace cgevap {
 // Records msg as the handle's last error (or the create error) and returns code.
 int sim_fail(cgevap_sim* s, int code, const std::string& msg);
 AuxArgs aux_of(const cgevap_sim* s);
+// Internal storage code (ST_*) of an API storage code (CGEVAP_*; -1 if unknown).
+int internal_storage(int api_storage);
+// True for the layouts that hold colour-blind populations and a recolouring record per cell.
+bool is_recolour_on_pull(int api_storage);
 // Arguments of one fused step of the current plan, reading state[cur] and writing state[cur^1].
 StepArgs step_args(cgevap_sim* s);
 // Site bytes read by the next step, recomputed from the current state: under the gradient rule

@@ -361,6 +361,67 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
   sb = acc.y;
 }
 
+// 16-bit recolour-on-pull layout: pull one cell.  Each moving population is decoded from its
+// 16-bit deviation and the source's rest-state scale Rf, f_i = fl(r_i Rf + dev / s), and split
+// with the source's record as pull_cell_rc does; recbox / refbox give the staged record and scale
+// of box position (y, x) in plane slot q.  The rest pair (f_0^r, f_0^b) is the cell's own, read
+// from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb)
+// summed rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact
+// sum of the split values.
+template <int Q, int S, class RecBox, class RefBox>
+__device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
+                                               PlaneOffsets po, uint32_t sbits, int ex, int ey,
+                                               const int (&ps)[3], const RecBox& recbox,
+                                               const RefBox& refbox, V2<float> (&g)[Q], float& sr,
+                                               float& sb, float& lr, float& lb) {
+  using L = Lattice<Q>;
+  using H = typename Storage<S>::half_t;
+  using P = typename H::packed;
+  const char* base = reinterpret_cast<const char*>(A.pin);
+  const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
+  const unsigned short* dev = reinterpret_cast<const unsigned short*>(base + lay.dev);
+  unsigned short raw[Q];
+  // all deviation loads first
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+    int dir = i;
+    if (sbits) {
+      const bool bounce = (sbits >> i) & 1u;
+      src = bounce ? si : src;
+      dir = bounce ? opp(i) : i;
+    }
+    raw[i] = __ldg(dev + (size_t)(dir - 1) * A.g.nstore + src);
+  }
+  const float2 r0 = __ldg(reinterpret_cast<const float2*>(base) + si);
+  g[0] = {r0.x + r0.y, 0.0f};
+  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
+  const float inv_scale = A.ph.inv_scale;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const bool bounce = sbits && ((sbits >> i) & 1u);
+    // the source's record and scale: box position x - c_i in plane m - c_i,m (own if bounced)
+    const int q = bounce ? ps[1] : ps[1 + L::cm(i)];
+    const int y = bounce ? ey : ey - L::cb(i), x = bounce ? ex : ex - L::ca(i);
+    const float4 rc = recbox(q, y, x);
+    const float rf = refbox(q, y, x);
+    P pv;
+    *reinterpret_cast<unsigned short*>(&pv) = raw[i];
+    const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
+    float cv = rc_cv<L>(i, rc);
+    if (bounce) cv = -cv;
+    const float fr = rc_red<L>(i, rc.x, f, cv);
+    fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
+    g[i] = {f, 0.0f};
+  }
+  sr = acc.x;
+  sb = acc.y;
+  lr = lo.x;
+  lb = lo.y;
+}
+
 template <class R>
 __device__ __forceinline__ void norm_pair(R F2, R& Fn, R& iFn);
 template <>
@@ -451,7 +512,20 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   const V2<R> f0{wr * fi0, fi0 - wr * fi0};
   float* const rc_pop = reinterpret_cast<float*>(A.pout);  // recolour-on-pull layout only
   (void)rc_pop;
-  if constexpr (Storage<S>::rc) {
+  // 16-bit recolour-on-pull: the record, the rest-state scale Rf = f_1^eq(rho, 0) and what the
+  // moving populations will deliver per colour, summed without rounding error (rc_out_hi + lo)
+  float4 rc16_rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float rc16_rf = 0.0f;
+  float2 rc_out_hi = make_float2(0.0f, 0.0f), rc_out_lo = make_float2(0.0f, 0.0f);
+  (void)rc16_rec;
+  (void)rc16_rf;
+  (void)rc_out_hi;
+  (void)rc_out_lo;
+  if constexpr (Storage<S>::rc16) {
+    const R gv = rcol * iFn * rho * (R(1) - abar);
+    rc16_rec = make_float4(wr, gv * Fa, gv * Fb, gv * Fm);
+    rc16_rf = restc[1];
+  } else if constexpr (Storage<S>::rc) {
     // colour-blind populations plus the record (w_r, V) from which the reader recolours:
     // kr_s (F.c_i) = s_|c| (c_i . V) with V = beta (rho_r rho_b / rho) (1 - abar) F / |F|
     const R gv = rcol * iFn * rho * (R(1) - abar);
@@ -516,7 +590,25 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
       fri = fma(wr, fi, kp);
       frj = fma(wr, fj, -kp);
     }
-    if constexpr (Storage<S>::rc) {
+    if constexpr (Storage<S>::rc16) {
+      // encode f - r_i Rf (s scaled) in 16 bits, decode as a reader will, and split the decoded
+      // values with this cell's record exactly as the readers will split them
+      using H = typename Storage<S>::half_t;
+      using P = typename H::packed;
+      const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
+      P* dev = reinterpret_cast<P*>(reinterpret_cast<char*>(A.pout) + lay.dev);
+      const float ri = float(rc16_ratio<L>(i)) * rc16_rf;  // exact (r_i is a power of two)
+      const P hi = H::pack((fi - ri) * ph.scale);
+      const P hj = H::pack((fj - ri) * ph.scale);
+      dev[(size_t)(i - 1) * A.g.nstore + si] = hi;
+      dev[(size_t)(j - 1) * A.g.nstore + si] = hj;
+      const float di = fmaf(H::unpack(hi), ph.inv_scale, ri);
+      const float dj = fmaf(H::unpack(hj), ph.inv_scale, ri);
+      const float fr_i = rc_red<L>(i, rc16_rec.x, di, rc_cv<L>(i, rc16_rec));
+      const float fr_j = rc_red<L>(j, rc16_rec.x, dj, rc_cv<L>(j, rc16_rec));
+      fast_two_sum_acc(rc_out_hi, rc_out_lo, make_float2(fr_i, di - fr_i));
+      fast_two_sum_acc(rc_out_hi, rc_out_lo, make_float2(fr_j, dj - fr_j));
+    } else if constexpr (Storage<S>::rc) {
       const size_t ns = (size_t)A.g.nstore;
       rc_pop[i * ns + si] = fi;
       rc_pop[j * ns + si] = fj;
@@ -553,6 +645,21 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
         }
       }
     }
+  }
+  if constexpr (Storage<S>::rc16) {
+    // the rest pair carries the exact colour masses (rr + lr, rb + lb) less what the moving
+    // populations deliver (rc_out_hi + rc_out_lo): TwoSum of the large terms, then the small ones
+    // (the periodic images of the TMA family are not kept for this layout)
+    const float2 t = make_float2(float(rr), float(rb));
+    const float2 s2 = sub2(t, rc_out_hi);
+    const float2 e2 = make_float2(two_sum_err(t.x, -rc_out_hi.x, s2.x),
+                                  two_sum_err(t.y, -rc_out_hi.y, s2.y));
+    const float2 small = __fadd2_rn(e2, sub2(make_float2(float(lr), float(lb)), rc_out_lo));
+    char* b = reinterpret_cast<char*>(A.pout);
+    const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
+    reinterpret_cast<float2*>(b)[si] = __fadd2_rn(s2, small);
+    reinterpret_cast<float4*>(b + lay.rec)[si] = rc16_rec;
+    reinterpret_cast<float*>(b + lay.ref)[si] = rc16_rf;
   }
   if constexpr (Storage<S>::dev) {
     // decoding gives f_i = f_0 kappa_i + deviation / scale, so raising f_0^k by delta raises the
@@ -641,9 +748,10 @@ struct TileSmem {
   static constexpr int TH = TY * CPT;
   static constexpr int HX = TX + 2, HY = L::D3 ? TH + 2 : 1;
   static constexpr bool DEV = Storage<S>::dev;
-  // source staging: rest pairs (deviation storages) or recolouring records (ST_RC)
-  static constexpr bool STAGE = DEV || S == ST_RC;
-  static constexpr int BOX = S == ST_RC ? 16 : 8;
+  // source staging: rest pairs (deviation storages), recolouring records (ST_RC), or records
+  // plus rest-state scales (16-bit recolour-on-pull)
+  static constexpr bool STAGE = DEV || Storage<S>::rc_in;
+  static constexpr int BOX = Storage<S>::rc_in ? (Storage<S>::rc16 ? 20 : 16) : 8;
   static constexpr int RX = STAGE ? TX + 4 : 1, RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1, RS = STAGE ? 4 : 1;
   // every part starts on a 16-byte boundary
   static constexpr int RING = ((4 * HY * HX * (int)sizeof(R)) + 15) & ~15;
@@ -684,7 +792,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   R(*ring)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ring_mem);
   // deviation storage: rest pairs of the tile plus a two-cell ring, planes m .. m+2
   constexpr bool DEV = Storage<S>::dev;
-  constexpr bool RCIN = S == ST_RC;      // reads the recolour-on-pull layout
+  constexpr bool RCIN = Storage<S>::rc_in;          // reads a recolour-on-pull layout
+  constexpr bool RC16IN = RCIN && Storage<S>::rc16;  // ... the 16-bit one
   constexpr bool STAGE = DEV || RCIN;    // pulls read per-source data staged in shared memory
   constexpr int RX = STAGE ? TX + 4 : 1;
   constexpr int RY = STAGE ? (L::D3 ? TH + 4 : 1) : 1;
@@ -758,13 +867,29 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   }
   const int plane_stride = G.rows * G.pitch;
   auto rest_slot = [&](int uq) { return (uq - m0 + 4) & 3; };
-  // ST_RC: the recolouring records (w_r, V) of the same box, staged the same way
+  // ST_RC: the recolouring records (w_r, V) of the same box, staged the same way; the 16-bit
+  // recolour-on-pull layout also stages the rest-state scales, in a second array
   float4(*rec_ring)[RY][RX] = reinterpret_cast<float4(*)[RY][RX]>(rest_mem);
+  float(*ref_ring)[RY][RX] = reinterpret_cast<float(*)[RY][RX]>(rest_mem + RS * RY * RX * 16);
+  (void)ref_ring;
   auto stage_rest = [&](int uq) {  // rest pairs / records of plane uq (unwrapped) into its slot
     if (!STAGE) return;
     const Plane q = make_plane(G, uq);
     const int sl = rest_slot(uq);
-    if constexpr (RCIN) {
+    if constexpr (RC16IN) {
+      const Rc16Layout lay = rc16_layout(Q, G.nstore);
+      const char* b = reinterpret_cast<const char*>(A.pin);
+      const float4* rec = reinterpret_cast<const float4*>(b + lay.rec);
+      const float* ref = reinterpret_cast<const float*>(b + lay.ref);
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int e = tid + k * NT;
+        if (e < RN && q.ok && rest_off[k] >= 0) {
+          rec_ring[sl][e / RX][e % RX] = __ldg(rec + q.m * plane_stride + rest_off[k]);
+          ref_ring[sl][e / RX][e % RX] = __ldg(ref + q.m * plane_stride + rest_off[k]);
+        }
+      }
+    } else if constexpr (RCIN) {
       const float4* rec = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(A.pin) +
                                                           rc_record_offset(Q, G.nstore));
 #pragma unroll
@@ -812,6 +937,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   };
   auto restbox = [&](int slot, int y, int x) -> float2 { return rest_ring[slot][y][x]; };
   auto recbox = [&](int slot, int y, int x) -> float4 { return rec_ring[slot][y][x]; };
+  auto refbox = [&](int slot, int y, int x) -> float { return ref_ring[slot][y][x]; };
 
   // The colour-blind sums of the next plane's pulled, post-exchange populations wait in
   // thread-private columns of shared memory (only this thread reads or writes its columns, so no
@@ -861,6 +987,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           if constexpr (DEV)
             pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                                 L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb, lr_unused, lb_unused);
+          else if constexpr (RC16IN)
+            pull_cell_rc16<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
+                                 L::D3 ? hy + 1 : 0, ps, recbox, refbox, tmp, sr, sb, lr_unused,
+                                 lb_unused);
           else
             pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                             L::D3 ? hy + 1 : 0, ps, recbox, tmp, sr, sb);
@@ -885,6 +1015,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                               L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c], out[c].rr,
                               out[c].rb, out[c].lr, out[c].lb);
+        else if constexpr (RC16IN)
+          pull_cell_rc16<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
+                               L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, refbox, g[c], out[c].rr,
+                               out[c].rb, out[c].lr, out[c].lb);
         else if constexpr (RCIN)
           pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                           L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c], out[c].rr, out[c].rb);
@@ -900,7 +1034,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           const R sr = out[c].rr, sb = out[c].rb;
           rn = exchange_from_sums<S>(A, cells[c], sr, sb, out[c].rr, out[c].rb, out[c].e,
                                      out[c].flags, out[c].irho);
-          if constexpr (DEV) {  // the exchange's own rounding joins the sums' (TwoSum)
+          if constexpr (DEV || RC16IN) {  // the exchange's own rounding joins the sums' (TwoSum)
             out[c].lr = __fadd_rn(out[c].lr, two_sum_err(sr, -out[c].e, out[c].rr));
             out[c].lb = __fadd_rn(out[c].lb, two_sum_err(sb, out[c].e, out[c].rb));
           }
@@ -974,7 +1108,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         }
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
-      if constexpr (DEV)
+      if constexpr (DEV || RC16IN)
         epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
                                 cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
                                 nloc, rem, cur[c].lr, cur[c].lb);

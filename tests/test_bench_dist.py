@@ -80,9 +80,37 @@ def test_reference_arm_line(oracle_lib):
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
     assert line["impl"] == "reference"
     assert line["unit"] == "MLUPS" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    cores, model = b.host_cpu()
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == cores
+    assert line["cpu_baseline"]["cpu_model"] == model
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["steps"] == 2 and line["warmup"] == 1
+
+
+def test_cpu_baseline_reports_all_cores_and_one(oracle_lib):
+    b = load_bench()
+    cb = b.cpu_baseline(target_s=0.05)
+    cores, model = b.host_cpu()
+    assert cb["kind"] == "oracle" and cb["cores"] == cores == cb["nproc"]
+    assert cb["cpu_model"] == model and cb["value"] > 0
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+
+
+def test_timing_build_computes_the_oracle_step(oracle_lib):
+    """The OpenMP build timed by the CPU baseline runs the same per-cell arithmetic as the pinned
+    single-thread oracle: equal populations bit for bit; the ledger's sum may differ only by the
+    order of its additions."""
+    import numpy as np
+    from paper_2412_14859_gb300 import inputs
+    b = load_bench()
+    case = inputs.shrink(inputs.sphere_3d(), (14, 13, 17), R0=4.5)
+    p = b.oracle_params(case)
+    f0 = oracle_lib.init(p, case.phase(), case.noise_array())
+    plain = oracle_lib.Run(p, f0).step(4)
+    omp = oracle_lib.Run(p, f0, omp=True).step(4)
+    assert np.array_equal(plain.f, omp.f)
+    assert np.array_equal(plain.mask, omp.mask)
+    assert omp.evaporated == pytest.approx(plain.evaporated, rel=1e-13)
 
 
 def test_adjoint_section_times_a_second_iteration(monkeypatch):

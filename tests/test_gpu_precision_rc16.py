@@ -1,0 +1,131 @@
+"""The mixed form with 16-bit recolour-on-pull storage (CGEVAP_F16RC / CGEVAP_BF16RC): per cell the
+colour-blind post-collision populations as FP16 / BF16 deviations from the lattice-weight rest
+state r_i Rf, an FP32 recolouring record (w_r, V), an FP32 rest pair; FP32 arithmetic and the
+FP64 ledger.
+
+Against the oracle on the parity cases (same seeded inputs, 10-30 steps, flux 1e-5): relative
+L-infinity of rho_r and rho_b <= 1e-5 for FP16 -- the bound of the mixed form -- and a stated,
+looser bound for BF16 (8 significand bits against FP16's 11); the site masks equal the oracle's
+wherever its decision value lies more than 1e-6 from the threshold (FP16).  Against the FP64
+path over 300 steps of the density-ratio-10 drop: relative red-mass error <= 1e-7 (each colour's
+mass is carried exactly through the step), and with the flux off the red mass is conserved to
+rounding of the rest pairs."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+from harness import gpu_sim, oracle_run, rel_linf
+from paper_2412_14859_gb300 import inputs
+from test_gpu_parity import CASES
+
+pytestmark = pytest.mark.gpu
+
+LINF = {"f16rc": 1e-5, "bf16rc": 1e-4}  # relative L-inf of the densities against the oracle
+MARGIN = {"f16rc": 1e-6, "bf16rc": 1e-5}  # mask compared where the decision is this far off
+
+
+@pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
+@pytest.mark.parametrize("name,case,steps", CASES, ids=[c[0] for c in CASES])
+def test_step_matches_oracle(name, case, steps, storage):
+    case = replace(case, phi=1e-5)
+    run = oracle_run(case, steps)
+    sim = gpu_sim(case, storage)
+    sim.step(steps)
+    g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
+    o = run.macros()
+    tol = LINF[storage]
+    assert rel_linf(g["rho_r"], o["rho_r"]) <= tol
+    assert rel_linf(g["rho_b"], o["rho_b"]) <= tol
+    assert np.max(np.abs(g["u"] - o["u"])) <= tol * 10
+    mask = sim.mask().cpu().numpy()
+    far = run.margin > MARGIN[storage]
+    assert np.array_equal(mask[far] & 1, run.mask[far])
+    led = sim.ledger()
+    assert led["steps"] == steps
+    assert led["evaporated"] == pytest.approx(run.evaporated, rel=2e-3)
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
+@pytest.mark.parametrize("q,shape,nvar", [(9, (1, 40, 130), 2), (19, (12, 21, 37), 5)])
+def test_every_variant_matches_oracle(storage, q, shape, nvar):
+    case = inputs.Case("variants", q, shape, R0=5.0, noise=1e-6, phi=1e-5, rho_r_in=2.0)
+    run = oracle_run(case, 6)
+    for v in range(nvar):
+        sim = gpu_sim(case, storage)
+        sim.tune(0, v)
+        sim.step(6)
+        g = sim.macros()
+        assert rel_linf(g["rho_r"].cpu().numpy(), run.macros()["rho_r"]) <= LINF[storage], v
+        assert rel_linf(g["rho_b"].cpu().numpy(), run.macros()["rho_b"]) <= LINF[storage], v
+        sim.close()
+
+
+def drop3d(phi=1e-5):
+    return inputs.Case("precision", 19, (40, 44, 48), rho_r_in=10.0, rho_b_in=1.0, tau_b=0.8,
+                       sigma=inputs.sigma_from_amplitude(0.005), R0=11.0, phi=phi, noise=1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
+def test_mass_and_density_vs_fp64(storage):
+    case = drop3d()
+    steps = 300
+    ref = gpu_sim(case, "f64")
+    ref.step(steps)
+    sim = gpu_sim(case, storage)
+    sim.step(steps)
+    a = {k: v.cpu().numpy() for k, v in sim.macros().items()}
+    b = {k: v.cpu().numpy() for k, v in ref.macros().items()}
+    mass_err = abs(a["rho_r"].sum() - b["rho_r"].sum()) / b["rho_r"].sum()
+    assert mass_err <= 1e-7, mass_err
+    assert rel_linf(a["rho_r"], b["rho_r"]) <= (1e-4 if storage == "f16rc" else 1e-3)
+    ea, eb = sim.ledger()["evaporated"], ref.ledger()["evaporated"]
+    assert ea == pytest.approx(eb, rel=5e-3)
+    m0 = case.rho_r_in * (1 + case.phase()).sum() / 2
+    # the red mass that left equals what the FP64 ledger of Eq. (exchange) says left
+    assert m0 - a["rho_r"].sum() == pytest.approx(ea, rel=1e-3)
+    sim.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
+def test_flux_off_conserves_each_colour(storage):
+    case = drop3d(phi=0.0)
+    sim = gpu_sim(case, storage)
+    sim.step(1)
+    m = sim.macros()
+    r0, b0 = float(m["rho_r"].sum()), float(m["rho_b"].sum())
+    sim.step(400)
+    m = sim.macros()
+    assert abs(float(m["rho_r"].sum()) - r0) <= 1e-8 * r0
+    assert abs(float(m["rho_b"].sum()) - b0) <= 1e-8 * b0
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
+@pytest.mark.parametrize("q,shape", [(9, (1, 36, 70)), (19, (9, 13, 22))])
+def test_imported_state_reads_back_and_steps(storage, q, shape):
+    """An imported state is held as FP32 pairs until the next step, so it reads back exactly (to
+    FP32); after a step the decoded state is within the storage rounding of the FP32 pair path."""
+    case = inputs.Case("import", q, shape, R0=4.0, noise=1e-6, rho_r_in=5.0, phi=1e-5)
+    sim = gpu_sim(case, storage)
+    f64 = gpu_sim(case, "f64")
+    got, want = sim.populations().cpu().numpy(), f64.populations().cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-7 * np.max(np.abs(want))
+    pairs = gpu_sim(case, "f32")
+    sim.step(2)
+    pairs.step(2)
+    a = sim.populations().cpu().numpy()
+    b = pairs.populations().cpu().numpy()
+    assert np.max(np.abs(a - b)) <= (1e-5 if storage == "f16rc" else 1e-4) * np.max(np.abs(b))
+    # set_populations of the decoded state, one more step each: the same again
+    sim.set_populations(torch.from_numpy(a).cuda())
+    sim.step(1)
+    pairs.step(1)
+    a = sim.populations().cpu().numpy()
+    b = pairs.populations().cpu().numpy()
+    assert np.max(np.abs(a - b)) <= (1e-5 if storage == "f16rc" else 1e-4) * np.max(np.abs(b))
+    for s in (sim, f64, pairs):
+        s.close()
