@@ -98,10 +98,15 @@ def fit_gradient(case, basis, a, a_t, storage, T, ckpt):
     return at.grad.cpu().numpy(), float(L.detach()), dVt, V.detach()
 
 
-def test_flux_fit_gradient_matches_central_differences():
-    case, basis, a, a_t = cap_problem("f64")
-    T = 200
-    grad, L0, dVt, V0 = fit_gradient(case, basis, a, a_t, "f64", T, 64)
+@pytest.mark.parametrize("shape,R0,T,ckpt", [((32, 64, 64), 12.0, 200, 64),
+                                             ((128, 256, 256), 48.0, 256, 16)],
+                         ids=["reduced_64x64x32", "full_256x256x128"])
+def test_flux_fit_gradient_matches_central_differences(shape, R0, T, ckpt):
+    """The 16-coefficient flux-fit gradient of the reverse sweep against central differences
+    (h = 1e-3) of the forward run with its site sets replayed, FP64: on a reduced cap and on the
+    full 256x256x128 box of the sessile-cap workload (R0 = 48, 256 steps)."""
+    case, basis, a, a_t = cap_problem("f64", shape, R0)
+    grad, L0, dVt, V0 = fit_gradient(case, basis, a, a_t, "f64", T, ckpt)
     # the base run's site sets, step by step
     rec = fresh(case, "f64")
     rec.set_flux(0.0, flux(case, basis, torch.tensor(a).cuda()).contiguous())
@@ -131,7 +136,10 @@ def test_flux_fit_gradient_matches_central_differences():
         e[k] = h
         fd[k] = (float(loss(replay(a + e), dVt)) - float(loss(replay(a - e), dVt))) / (2 * h)
     err = np.max(np.abs(grad - fd)) / np.max(np.abs(fd))
+    print(f"{shape}: adjoint vs central differences {err:.2e}")
     assert err <= 1e-4, (err, grad, fd)
+    del masks
+    torch.cuda.empty_cache()
 
 
 def test_fp32_adjoint_close_to_fp64():

@@ -196,3 +196,32 @@ def test_paused_member_keeps_its_state():
         assert sim.ledger()["steps"] == n
         ref.close()
     ens.close()
+
+
+def test_benchmark_mix_members_equal_standalone_and_oracle():
+    """The 64-member ensemble the benchmark times (48 D2Q9 drops with sides 96-256, 16 D3Q19 drops
+    with sides 52-120; uneven flux, density ratio and threshold; FP32) after 10 steps of one
+    persistent launch per call: every member equals its standalone run within the FP32 parity
+    tolerance, and the smallest D2Q9 and D3Q19 members equal the oracle within it too."""
+    from paper_2412_14859_gb300.binding import Ensemble
+    cases = inputs.ensemble_members()
+    assert sum(c.q == 9 for c in cases) == 48 and sum(c.q == 19 for c in cases) == 16
+    ens = Ensemble(cases)
+    for sim, case in zip(ens.members, cases):
+        init_member(sim, case)
+    ens.step(4).step(6)
+    ens.status()
+    for sim, case in zip(ens.members, cases):
+        ref = gpu_sim(case, "f32")
+        ref.step(10)
+        a, b = sim.populations(torch.float32), ref.populations(torch.float32)
+        assert (a - b).abs().max().item() <= 1e-5 * b.abs().max().item(), case.name
+        assert sim.ledger()["steps"] == 10
+        ref.close()
+    for q in (9, 19):
+        j = min((k for k, c in enumerate(cases) if c.q == q), key=lambda k: cases[k].ncell)
+        run = oracle_run(cases[j], 10)
+        g = ens.members[j].macros()
+        assert rel_linf(g["rho_r"].cpu().numpy(), run.macros()["rho_r"]) <= 1e-5, cases[j].name
+        assert rel_linf(g["rho_b"].cpu().numpy(), run.macros()["rho_b"]) <= 1e-5, cases[j].name
+    ens.close()
