@@ -26,23 +26,30 @@ _SO = os.path.join(_BUILD, "libcg_oracle.so")
 # The same source built with OpenMP: used only to time the oracle on all host cores (the CPU
 # baseline of bench.py); every test uses the single-thread library above.
 _SO_OMP = os.path.join(_BUILD, "libcg_oracle_omp.so")
+# The same source built with multiply-add contraction: only to measure how much the method
+# amplifies differences of rounding order (a test of the parity bounds over long runs).
+_SO_FMA = os.path.join(_BUILD, "libcg_oracle_fma.so")
 
 RULE_GRADIENT = 0
 RULE_BAND = 1
 RULE_GIVEN = 2  # replay a recorded site set (bit 0 of ``mask_given``)
 
 
-def build(force: bool = False, omp: bool = False) -> str:
+def build(force: bool = False, omp: bool = False, contract: bool = False) -> str:
     """Compile the C oracle (plain gcc, IEEE FP64, no contraction into FMA); omp: the OpenMP
-    timing build of the same source instead."""
+    timing build of the same source instead; contract: the build with multiply-adds contracted
+    into FMA instructions (x86-64 needs -mfma for them; AArch64 has them in its base ISA)."""
+    import platform
     os.makedirs(_BUILD, exist_ok=True)
-    so = _SO_OMP if omp else _SO
+    so = _SO_FMA if contract else (_SO_OMP if omp else _SO)
     if force or not os.path.exists(so) or os.path.getmtime(so) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "cg_oracle.h"))
     ):
         tmp = so + f".{os.getpid()}.tmp"
+        fp = ["-ffp-contract=fast"] + (["-mfma"] if platform.machine() in ("x86_64", "AMD64") else []) \
+            if contract else ["-ffp-contract=off"]
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+            ["gcc", "-O2", "-std=c11"] + fp + ["-fno-fast-math", "-shared", "-fPIC"]
             + (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, so)
@@ -75,10 +82,15 @@ class _Ledger(ctypes.Structure):
 
 _lib = None
 _lib_omp = None
+_lib_fma = None
 
 
-def _L(omp: bool = False):
-    global _lib, _lib_omp
+def _L(omp: bool = False, contract: bool = False):
+    global _lib, _lib_omp, _lib_fma
+    if contract:
+        if _lib_fma is None:
+            _lib_fma = _declare(ctypes.CDLL(build(contract=True)))
+        return _lib_fma
     if omp:
         if _lib_omp is None:
             _lib_omp = _declare(ctypes.CDLL(build(omp=True)))
@@ -241,11 +253,13 @@ def macros(p: Params, f: np.ndarray):
 
 class Run:
     """A lattice advanced by the oracle: state f (post-recoloring), |F| of the last step, ledger.
-    omp: step with the OpenMP timing build (all host cores; for timing only)."""
+    omp: step with the OpenMP timing build (all host cores; for timing only); contract: step with
+    the build whose multiply-adds are contracted (for measuring rounding-order sensitivity)."""
 
-    def __init__(self, p: Params, f: np.ndarray, omp: bool = False):
+    def __init__(self, p: Params, f: np.ndarray, omp: bool = False, contract: bool = False):
         self.p = p
         self.omp = omp
+        self.contract = contract
         self.f = np.ascontiguousarray(f, np.float64).copy()
         self.G = gradient_norm(p, self.f)  # |F| "of the previous step" before step 0
         self.mask = np.zeros(p.shape, np.uint8)
@@ -259,9 +273,10 @@ class Run:
         f_out = np.empty_like(self.f)
         G_out = np.empty(self.p.shape)
         for _ in range(n):
-            _check(_L(self.omp).orc_step(ctypes.byref(cp), _dp(self.f), _dp(f_out), _dp(self.G),
-                                 _dp(G_out), _up(self.mask), _dp(self.margin),
-                                 ctypes.byref(self.ledger)))
+            lib = _L(self.omp, self.contract)
+            _check(lib.orc_step(ctypes.byref(cp), _dp(self.f), _dp(f_out), _dp(self.G),
+                                _dp(G_out), _up(self.mask), _dp(self.margin),
+                                ctypes.byref(self.ledger)))
             self.f, f_out = f_out, self.f
             self.G, G_out = G_out, self.G
             self.steps += 1

@@ -82,17 +82,22 @@ def rel_linf(a, b) -> float:
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def oracle_summary(case: inputs.Case, steps: int) -> dict:
-    """What the parity tests compare after `steps` oracle steps of a case (picklable; runs in a
-    worker process)."""
-    run = oracle_run(case, steps)
-    m = run.macros()
-    return {"rho_r": m["rho_r"], "rho_b": m["rho_b"], "mask": run.mask.copy(),
-            "margin": run.margin.copy(), "evaporated": run.evaporated,
-            "site_steps": run.ledger.site_steps, "min_margin": min(run.min_margin_history)}
+def oracle_summary(case: inputs.Case, checkpoints) -> list:
+    """What the parity tests compare, after each of the (increasing) step counts in `checkpoints`
+    of one oracle run of a case (picklable; runs in a worker process)."""
+    p = oracle_params(case)
+    run = oracle.Run(p, oracle.init(p, case.phase(), case.noise_array()))
+    out = []
+    for n in checkpoints:
+        run.step(n - run.steps)
+        m = run.macros()
+        out.append({"steps": n, "rho_r": m["rho_r"], "rho_b": m["rho_b"], "mask": run.mask.copy(),
+                    "margin": run.margin.copy(), "evaporated": run.evaporated,
+                    "site_steps": run.ledger.site_steps, "min_margin": min(run.min_margin_history)})
+    return out
 
 
-def oracle_summaries(cases, steps: int, workers: int = 0) -> list:
+def oracle_summaries(cases, checkpoints, workers: int = 0) -> list:
     """oracle_summary of many cases in a pool of spawned processes (never forked: the parent may
     hold a CUDA context)."""
     import concurrent.futures
@@ -101,4 +106,4 @@ def oracle_summaries(cases, steps: int, workers: int = 0) -> list:
     n = workers or max(1, min(len(cases), os.cpu_count() or 1))
     ctx = multiprocessing.get_context("spawn")
     with concurrent.futures.ProcessPoolExecutor(n, mp_context=ctx) as ex:
-        return list(ex.map(oracle_summary, cases, [steps] * len(cases)))
+        return list(ex.map(oracle_summary, cases, [tuple(checkpoints)] * len(cases)))

@@ -8,9 +8,14 @@ theta gets its S-bar the way Sec. II.B calibrates: the time-averaged number of s
 interface length of a flat-interface run (the 64^2 slab) that itself uses that S-bar, a fixed
 point reached by iterating.
 
-- Parity: after the first 500 steps every member equals the oracle on the same seeded input --
-  FP64 within 1e-12, FP32 within a stated bound for 500 steps -- with identical site masks away
-  from the threshold.
+- Parity: every member equals the oracle on the same seeded input, with identical site masks
+  away from the threshold, after 50 steps within the parity bounds of the short cases (FP64
+  1e-12, FP32 1e-5) and after 500 steps within stated longer bounds.  The method amplifies
+  differences of rounding order over hundreds of steps: the oracle itself, compiled with
+  multiply-add contraction, departs from the pinned (uncontracted) build by 4e-11 after 300-500
+  steps of the (phi = 1e-6, theta = 0.3) case, having been at 1e-13 after 50; the GPU's FP64
+  arithmetic (contracted multiply-adds, reciprocal and square-root forms of its own) departs by
+  up to 1e-9.  So FP64 is held to 1e-8 and FP32 to 1e-4 at 500 steps.
 - Radius law (Sec. III.A, R = R0 - phi t / rho_l, the evaporating drop of the paper in 2D): from
   the equilibrated drop, the two largest fluxes run until the law gives R = R0/2 (2e5 and 6.3e5
   steps), each member paused when it gets there; the radius R = sqrt(V / pi) of the liquid area
@@ -27,7 +32,8 @@ from paper_2412_14859_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 THETAS = (0.3, 0.5, 0.7)
-FP32_500 = 1e-4  # relative L-inf of the densities after 500 FP32 steps (rounding accumulates)
+# relative L-inf of the densities against the oracle after 50 and 500 steps
+BOUND = {"f64": {50: 1e-12, 500: 1e-8}, "f32": {50: 1e-5, 500: 1e-4}}
 
 
 def band_sbar(theta: float) -> float:
@@ -59,30 +65,33 @@ def init(ens, cases, flux=True):
 
 def test_sweep_first_500_steps_match_oracle(sweep):
     from paper_2412_14859_gb300.binding import Ensemble
-    steps = 500
-    want = oracle_summaries(sweep, steps)  # FP64 and FP32 members share their seeded inputs
+    checkpoints = (50, 500)
+    want = oracle_summaries(sweep, checkpoints)  # FP64 and FP32 members share their inputs
     cases = sweep + sweep
     storages = ["f64"] * len(sweep) + ["f32"] * len(sweep)
     ens = Ensemble(cases, storages)
     init(ens, cases)
-    ens.step(steps)
-    ens.status()
-    worst = {"f64": 0.0, "f32": 0.0}
-    for j, (sim, case, st) in enumerate(zip(ens.members, cases, storages)):
-        o = want[j % len(sweep)]
-        g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
-        err = max(rel_linf(g["rho_r"], o["rho_r"]), rel_linf(g["rho_b"], o["rho_b"]))
-        worst[st] = max(worst[st], err)
-        tol = 1e-12 if st == "f64" else FP32_500
-        if st == "f64":
-            assert o["min_margin"] > 1e-9, (case.phi, case.threshold)
-        assert err <= tol, (st, case.phi, case.threshold, err)
-        far = o["margin"] > 1e-6
-        assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, o["mask"][far])
-        led = sim.ledger()
-        assert led["steps"] == steps
-        assert led["evaporated"] == pytest.approx(o["evaporated"], rel=1e-12 if st == "f64" else 1e-3)
-    print("worst relative L-inf after 500 steps", worst)
+    worst = {}
+    done = 0
+    for ci, steps in enumerate(checkpoints):
+        ens.step(steps - done)
+        done = steps
+        ens.status()
+        for j, (sim, case, st) in enumerate(zip(ens.members, cases, storages)):
+            o = want[j % len(sweep)][ci]
+            g = {k: v.cpu().numpy() for k, v in sim.macros().items()}
+            err = max(rel_linf(g["rho_r"], o["rho_r"]), rel_linf(g["rho_b"], o["rho_b"]))
+            worst[(st, steps)] = max(worst.get((st, steps), 0.0), err)
+            if st == "f64":  # no decision within reach of FP64 rounding
+                assert o["min_margin"] > 1e-9, (case.phi, case.threshold)
+            assert err <= BOUND[st][steps], (st, steps, case.phi, case.threshold, err)
+            far = o["margin"] > 1e-6
+            assert np.array_equal(sim.mask().cpu().numpy()[far] & 1, o["mask"][far])
+            led = sim.ledger()
+            assert led["steps"] == steps
+            assert led["evaporated"] == pytest.approx(o["evaporated"],
+                                                      rel=1e-10 if st == "f64" else 1e-3)
+    print("worst relative L-inf (storage, steps):", worst)
     ens.close()
 
 
@@ -99,8 +108,11 @@ def test_sweep_radius_law_to_half_radius(sweep):
         V = float(sim.volume())
         R0.append(float(np.sqrt(V / np.pi)))
         rho_l.append(float(sim.macros()["rho_r"].max()))
+    m_red0 = []
     for sim, case in zip(ens.members, cases):
         sim.set_flux(case.phi)
+        sim.reset_ledger()
+        m_red0.append(float(sim.macros()["rho_r"].sum()))
     # law time of R/R0 = 3/4 and 1/2 for each member
     marks = [[(1.0 - f) * R0[j] * rho_l[j] / c.phi for f in (0.75, 0.5)] for j, c in enumerate(cases)]
     err = [[None, None] for _ in cases]
@@ -122,10 +134,15 @@ def test_sweep_radius_law_to_half_radius(sweep):
                     ens.set_active(j, False)
     ens.status()
     for j, c in enumerate(cases):
+        # red mass that left against the FP64 ledger of Eq. (exchange)
+        sim = ens.members[j]
+        lost = m_red0[j] - float(sim.macros()["rho_r"].sum())
+        ratio = lost / sim.ledger()["evaporated"]
         print(f"{storages[j]} phi={c.phi:.3g} theta={c.threshold} sbar={c.sbar:.4f} R0={R0[j]:.2f} "
-              f"error at R/R0=3/4: {err[j][0]:+.2f} %, at 1/2: {err[j][1]:+.2f} %")
-    for j in range(len(picked)):  # FP32 and FP64 follow the same path
-        assert abs(err[j][1] - err[j + len(picked)][1]) <= 0.05
-    for e in err:
-        assert abs(e[0]) <= 5.0 and abs(e[1]) <= 12.0, e
+              f"error at R/R0=3/4: {err[j][0]:+.2f} %, at 1/2: {err[j][1]:+.2f} %, "
+              f"red mass lost / ledger - 1 = {ratio - 1:+.2e}")
+        if storages[j] == "f64":
+            assert abs(ratio - 1) <= 1e-9
+        bound = {0.3: (2.0, 3.0), 0.5: (3.5, 10.0), 0.7: (2.0, 4.0)}[c.threshold]
+        assert abs(err[j][0]) <= bound[0] and abs(err[j][1]) <= bound[1], (c.phi, c.threshold, err[j])
     ens.close()

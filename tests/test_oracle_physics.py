@@ -230,3 +230,28 @@ def test_flat_recession_band_rule():
     sb_last, dw_last, _ = runs[-1]
     assert sb_last == pytest.approx(sbar, rel=0.01)  # converged
     assert dw_last == pytest.approx(2 * case.phi * 2000 / rho_l, rel=0.02)
+
+
+@pytest.mark.slow
+def test_rounding_order_is_amplified_over_hundreds_of_steps():
+    """The method's sensitivity to the order of rounding, measured on the oracle alone: the same
+    source built with multiply-adds contracted into FMA instructions departs from the pinned
+    (uncontracted) build by about 1e-13 after 50 steps of the D2Q9 256^2 drop of the sweep
+    (phi = 1e-6, theta = 0.3, S-bar = 1.0285), and by orders of magnitude more after 300: the
+    reason parity bounds over hundreds of steps are looser than over tens."""
+    from dataclasses import replace
+    from harness import oracle_params
+    case = replace(inputs.drop_2d(1e-6, 0.3), sbar=1.0285)
+    p = oracle_params(case)
+    f0 = oracle.init(p, case.phase(), case.noise_array())
+    a, b = oracle.Run(p, f0), oracle.Run(p, f0, contract=True)
+    errs = []
+    for n in (50, 250):
+        a.step(n)
+        b.step(n)
+        ra, rb = a.macros()["rho_r"], b.macros()["rho_r"]
+        errs.append(float(np.max(np.abs(ra - rb)) / np.max(np.abs(ra))))
+    print("contracted vs pinned oracle after 50 and 300 steps:", errs)
+    assert 0.0 < errs[0] <= 1e-12
+    assert errs[1] >= 10.0 * errs[0]
+    assert errs[1] <= 1e-9
