@@ -363,58 +363,83 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
 
 // 16-bit recolour-on-pull layout: pull one cell.  Each moving population is decoded from its
 // 16-bit deviation and the source's rest-state scale Rf, f_i = fl(r_i Rf + dev / s), and split
-// with the source's record as pull_cell_rc does; recbox / refbox give the staged record and scale
-// of box position (y, x) in plane slot q.  The rest pair (f_0^r, f_0^b) is the cell's own, read
-// from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb)
-// summed rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact
-// sum of the split values.
-template <int Q, int S, class RecBox, class RefBox>
+// with the source's record as pull_cell_rc does.  rec[k] / ref[k] point at this cell's position
+// (its box row and column) in the staged record and scale boxes of plane m + 1 - k, the plane
+// the pull sources of the directions with c_m = k - 1 lie in (k = 1: this plane), so the source
+// of direction i sits at the compile-time offset -(c_i,b RX + c_i,a) from rec[1 + c_i,m].  The rest pair
+// (f_0^r, f_0^b) is the cell's own, read from global memory.  Output as pull_cell_dev: g_i =
+// (f_i, 0), the colour totals (sr, sb) summed rest pair first with Fast2Sum, and their rounding
+// errors (lr, lb): sr + lr is the exact sum of the split values.  A cell none of whose links
+// bounces back (sbits == 0, nearly every cell) takes a path whose addresses are all fixed
+// offsets; the others take the general one.
+template <int Q, int S, int RX>
 __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
-                                               PlaneOffsets po, uint32_t sbits, int ex, int ey,
-                                               const int (&ps)[3], const RecBox& recbox,
-                                               const RefBox& refbox, V2<float> (&g)[Q], float& sr,
-                                               float& sb, float& lr, float& lb) {
+                                               PlaneOffsets po, uint32_t sbits,
+                                               const float4* const (&rec)[3],
+                                               const float* const (&ref)[3], V2<float> (&g)[Q],
+                                               float& sr, float& sb, float& lr, float& lb) {
   using L = Lattice<Q>;
   using H = typename Storage<S>::half_t;
   using P = typename H::packed;
   const char* base = reinterpret_cast<const char*>(A.pin);
   const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
   const unsigned short* dev = reinterpret_cast<const unsigned short*>(base + lay.dev);
+  const int ns = A.g.nstore;
   unsigned short raw[Q];
-  // all deviation loads first
+  const float inv_scale = A.ph.inv_scale;
+  float2 acc, lo = make_float2(0.0f, 0.0f);
+  if (sbits == 0) {
+    // all deviation loads first
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
-              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
-              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
-    int dir = i;
-    if (sbits) {
+    for (int i = 1; i < Q; ++i) {
+      const int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                      (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                      (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+      raw[i] = __ldg(dev + (i - 1) * ns + src);
+    }
+    acc = __ldg(reinterpret_cast<const float2*>(base) + si);
+    g[0] = {acc.x + acc.y, 0.0f};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int off = -(L::cb(i) * RX + L::ca(i));
+      const float4 rc = rec[1 + L::cm(i)][off];
+      const float rf = ref[1 + L::cm(i)][off];
+      P pv;
+      *reinterpret_cast<unsigned short*>(&pv) = raw[i];
+      const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
+      const float fr = rc_red<L>(i, rc.x, f, rc_cv<L>(i, rc));
+      fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
+      g[i] = {f, 0.0f};
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
       const bool bounce = (sbits >> i) & 1u;
       src = bounce ? si : src;
-      dir = bounce ? opp(i) : i;
+      const int dir = bounce ? opp(i) : i;
+      raw[i] = __ldg(dev + (size_t)(dir - 1) * ns + src);
     }
-    raw[i] = __ldg(dev + (size_t)(dir - 1) * A.g.nstore + src);
-  }
-  const float2 r0 = __ldg(reinterpret_cast<const float2*>(base) + si);
-  g[0] = {r0.x + r0.y, 0.0f};
-  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
-  const float inv_scale = A.ph.inv_scale;
+    acc = __ldg(reinterpret_cast<const float2*>(base) + si);
+    g[0] = {acc.x + acc.y, 0.0f};
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const bool bounce = sbits && ((sbits >> i) & 1u);
-    // the source's record and scale: box position x - c_i in plane m - c_i,m (own if bounced)
-    const int q = bounce ? ps[1] : ps[1 + L::cm(i)];
-    const int y = bounce ? ey : ey - L::cb(i), x = bounce ? ex : ex - L::ca(i);
-    const float4 rc = recbox(q, y, x);
-    const float rf = refbox(q, y, x);
-    P pv;
-    *reinterpret_cast<unsigned short*>(&pv) = raw[i];
-    const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
-    float cv = rc_cv<L>(i, rc);
-    if (bounce) cv = -cv;
-    const float fr = rc_red<L>(i, rc.x, f, cv);
-    fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
-    g[i] = {f, 0.0f};
+    for (int i = 1; i < Q; ++i) {
+      const bool bounce = (sbits >> i) & 1u;
+      // the source's record and scale (the cell's own for a bounced link)
+      const int off = -(L::cb(i) * RX + L::ca(i));
+      const float4 rc = bounce ? rec[1][0] : rec[1 + L::cm(i)][off];
+      const float rf = bounce ? ref[1][0] : ref[1 + L::cm(i)][off];
+      P pv;
+      *reinterpret_cast<unsigned short*>(&pv) = raw[i];
+      const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
+      float cv = rc_cv<L>(i, rc);
+      if (bounce) cv = -cv;
+      const float fr = rc_red<L>(i, rc.x, f, cv);
+      fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
+      g[i] = {f, 0.0f};
+    }
   }
   sr = acc.x;
   sb = acc.y;
@@ -937,7 +962,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   };
   auto restbox = [&](int slot, int y, int x) -> float2 { return rest_ring[slot][y][x]; };
   auto recbox = [&](int slot, int y, int x) -> float4 { return rec_ring[slot][y][x]; };
-  auto refbox = [&](int slot, int y, int x) -> float { return ref_ring[slot][y][x]; };
 
   // The colour-blind sums of the next plane's pulled, post-exchange populations wait in
   // thread-private columns of shared memory (only this thread reads or writes its columns, so no
@@ -987,10 +1011,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           if constexpr (DEV)
             pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                                 L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb, lr_unused, lb_unused);
-          else if constexpr (RC16IN)
-            pull_cell_rc16<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
-                                 L::D3 ? hy + 1 : 0, ps, recbox, refbox, tmp, sr, sb, lr_unused,
-                                 lb_unused);
+          else if constexpr (RC16IN) {
+            const int ex = hx + 1, ey = L::D3 ? hy + 1 : 0;
+            const float4* const rp[3] = {&rec_ring[ps[0]][ey][ex], &rec_ring[ps[1]][ey][ex],
+                                         &rec_ring[ps[2]][ey][ex]};
+            const float* const fp[3] = {&ref_ring[ps[0]][ey][ex], &ref_ring[ps[1]][ey][ex],
+                                        &ref_ring[ps[2]][ey][ex]};
+            pull_cell_rc16<Q, S, RX>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, rp, fp, tmp, sr, sb,
+                                     lr_unused, lb_unused);
+          }
           else
             pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                             L::D3 ? hy + 1 : 0, ps, recbox, tmp, sr, sb);
@@ -1015,10 +1044,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           pull_cell_dev<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                               L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c], out[c].rr,
                               out[c].rb, out[c].lr, out[c].lb);
-        else if constexpr (RC16IN)
-          pull_cell_rc16<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
-                               L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, refbox, g[c], out[c].rr,
-                               out[c].rb, out[c].lr, out[c].lb);
+        else if constexpr (RC16IN) {
+          const int ex = lx + 2, ey = L::D3 ? ly0 + c * TY + 2 : 0;
+          const float4* const rp[3] = {&rec_ring[ps[0]][ey][ex], &rec_ring[ps[1]][ey][ex],
+                                       &rec_ring[ps[2]][ey][ex]};
+          const float* const fp[3] = {&ref_ring[ps[0]][ey][ex], &ref_ring[ps[1]][ey][ex],
+                                      &ref_ring[ps[2]][ey][ex]};
+          pull_cell_rc16<Q, S, RX>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, rp, fp, g[c],
+                                   out[c].rr, out[c].rb, out[c].lr, out[c].lb);
+        }
         else if constexpr (RCIN)
           pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
                           L::D3 ? ly0 + c * TY + 2 : 0, ps, recbox, g[c], out[c].rr, out[c].rb);
@@ -1068,7 +1102,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
-      for (int i = 0; i < Q; ++i) parked[(c * Q + i) * NT + tid] = g[c][i].r + g[c][i].b;
+      for (int i = 0; i < Q; ++i)
+        parked[(c * Q + i) * NT + tid] = STAGE ? g[c][i].r : g[c][i].r + g[c][i].b;
   }
   if (STAGE) __syncthreads();  // the first fill below restages a slot the pulls above read
 
@@ -1088,7 +1123,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         own[i] = parked[(c * Q + i) * NT + tid];
-        parked[(c * Q + i) * NT + tid] = g[c][i].r + g[c][i].b;
+        // staged storages deliver colour-blind values (g_i.b = 0): park them as they are
+        parked[(c * Q + i) * NT + tid] = STAGE ? g[c][i].r : g[c][i].r + g[c][i].b;
       }
       if (!(active[c] && cur[c].ok)) continue;
       const int ly = ly0 + c * TY;
