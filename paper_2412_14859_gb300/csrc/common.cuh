@@ -195,13 +195,23 @@ struct RcIO {
 // population is the same bits wherever it is computed (c_opp(i) . V is exactly -(c_i . V)).
 template <class L>
 __device__ __forceinline__ float rc_cv(int i, const float4& r) {
+  // the first nonzero term starts the sum (no addition to zero); i is a compile-time constant
+  // in every caller, so only the terms of direction i remain
   float cv = 0.0f;
-  if (L::ca(i) > 0) cv += r.y;
-  if (L::ca(i) < 0) cv -= r.y;
-  if (L::cb(i) > 0) cv += r.z;
-  if (L::cb(i) < 0) cv -= r.z;
-  if (L::cm(i) > 0) cv += r.w;
-  if (L::cm(i) < 0) cv -= r.w;
+  bool any = false;
+  if (L::ca(i) != 0) {
+    cv = L::ca(i) > 0 ? r.y : -r.y;
+    any = true;
+  }
+  if (L::cb(i) != 0) {
+    const float t = L::cb(i) > 0 ? r.z : -r.z;
+    cv = any ? cv + t : t;
+    any = true;
+  }
+  if (L::cm(i) != 0) {
+    const float t = L::cm(i) > 0 ? r.w : -r.w;
+    cv = any ? cv + t : t;
+  }
   return cv;
 }
 

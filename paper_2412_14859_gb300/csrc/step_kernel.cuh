@@ -267,37 +267,56 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
   const Physics& ph = A.ph;
   const P* dev = reinterpret_cast<const P*>(reinterpret_cast<const char*>(A.pin) +
                                             dev_block_offset(A.g.nstore));
+  const int ns = A.g.nstore;
   uint32_t raw[Q];
-  // all deviation loads first
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
-              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
-              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
-    int dir = i;
-    if (sbits) {
-      const bool bounce = (sbits >> i) & 1u;
-      src = bounce ? si : src;
-      dir = bounce ? opp(i) : i;
-    }
-    const P v = __ldg(dev + (size_t)(dir - 1) * A.g.nstore + src);
-    raw[i] = *reinterpret_cast<const uint32_t*>(&v);
-  }
   const float2 r0 = restbox(ps[1], ey, ex);
   g[0] = {r0.x + r0.y, 0.0f};
   float2 acc = r0, lo = make_float2(0.0f, 0.0f);
+  if (sbits == 0) {  // no link bounces back: every address is a fixed offset
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const bool bounce = sbits && ((sbits >> i) & 1u);
-    // the source's rest pair: box position x - c_i in plane m - c_i,m (own cell if bounced)
-    const float2 rs = bounce ? r0 : restbox(ps[1 + L::cm(i)], ey - L::cb(i), ex - L::ca(i));
-    P pv;
-    *reinterpret_cast<uint32_t*>(&pv) = raw[i];
-    const float2 d = Storage<S>::unpack(pv);
-    const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
-                                __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
-    fast_two_sum_acc(acc, lo, v);
-    g[i] = {v.x + v.y, 0.0f};
+    for (int i = 1; i < Q; ++i) {
+      const int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                      (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                      (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+      const P v = __ldg(dev + (i - 1) * ns + src);
+      raw[i] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const float2 rs = restbox(ps[1 + L::cm(i)], ey - L::cb(i), ex - L::ca(i));
+      P pv;
+      *reinterpret_cast<uint32_t*>(&pv) = raw[i];
+      const float2 d = Storage<S>::unpack(pv);
+      const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
+                                  __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
+      fast_two_sum_acc(acc, lo, v);
+      g[i] = {v.x + v.y, 0.0f};
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+      const bool bounce = (sbits >> i) & 1u;
+      src = bounce ? si : src;
+      const int dir = bounce ? opp(i) : i;
+      const P v = __ldg(dev + (size_t)(dir - 1) * ns + src);
+      raw[i] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const bool bounce = (sbits >> i) & 1u;
+      // the source's rest pair: box position x - c_i in plane m - c_i,m (own cell if bounced)
+      const float2 rs = bounce ? r0 : restbox(ps[1 + L::cm(i)], ey - L::cb(i), ex - L::ca(i));
+      P pv;
+      *reinterpret_cast<uint32_t*>(&pv) = raw[i];
+      const float2 d = Storage<S>::unpack(pv);
+      const float2 v = __ffma2_rn(rs, make_float2(ph.kap_r[i], ph.kap_b[i]),
+                                  __fmul2_rn(d, make_float2(ph.inv_scale, ph.inv_scale)));
+      fast_two_sum_acc(acc, lo, v);
+      g[i] = {v.x + v.y, 0.0f};
+    }
   }
   sr = acc.x;
   sb = acc.y;
@@ -319,20 +338,28 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
                                              V2<float> (&g)[Q], float& sr, float& sb) {
   using L = Lattice<Q>;
   const float* pop = reinterpret_cast<const float*>(A.pin);
+  const int ns = A.g.nstore;
   float fv[Q];
-  // all population loads first
+  // all population loads first (fixed offsets unless a link bounces back)
+  if (sbits == 0) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
-              (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
-              (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
-    int dir = i;
-    if (sbits) {
+    for (int i = 0; i < Q; ++i) {
+      const int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                      (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                      (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
+      fv[i] = __ldg(pop + i * ns + src);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
+                (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
+                (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
       const bool bounce = (sbits >> i) & 1u;
       src = bounce ? si : src;
-      dir = bounce ? opp(i) : i;
+      const int dir = bounce ? opp(i) : i;
+      fv[i] = __ldg(pop + (size_t)dir * ns + src);
     }
-    fv[i] = __ldg(pop + (size_t)dir * A.g.nstore + src);
   }
   const float4 r0 = recbox(ps[1], ey, ex);
   float2 acc;

@@ -31,7 +31,7 @@ static KernelRef pick(int q, int variant) {
       case 1: return rc16_ref<19, S, 32, 4, 4, 1>();
       case 2: return rc16_ref<19, S, 32, 4, 3, 1>();
       case 3: return rc16_ref<19, S, 16, 4, 8, 1>();
-      case 4: return rc16_ref<19, S, 16, 8, 3, 1>();
+      case 4: return rc16_ref<19, S, 32, 8, 2, 1>();  // 256 threads: a smaller ring per cell
     }
   } else if (q == 9) {
     switch (variant) {
