@@ -202,11 +202,18 @@ struct Half16 {
   using packed = __half;
   static __device__ __forceinline__ float unpack(packed p) { return __half2float(p); }
   static __device__ __forceinline__ packed pack(float v) { return __float2half_rn(v); }
+  // the raw 16 bits, in and out of a register without going through memory
+  static __device__ __forceinline__ float unpack_bits(unsigned short u) {
+    return __half2float(__ushort_as_half(u));
+  }
 };
 struct BHalf16 {
   using packed = __nv_bfloat16;
   static __device__ __forceinline__ float unpack(packed p) { return __bfloat162float(p); }
   static __device__ __forceinline__ packed pack(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float unpack_bits(unsigned short u) {
+    return __bfloat162float(__ushort_as_bfloat16(u));
+  }
 };
 template <class H, bool PAIRS_IN>
 struct Rc16Storage {

@@ -390,24 +390,23 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
 
 // 16-bit recolour-on-pull layout: pull one cell.  Each moving population is decoded from its
 // 16-bit deviation and the source's rest-state scale Rf, f_i = fl(r_i Rf + dev / s), and split
-// with the source's record as pull_cell_rc does.  rec[k] / ref[k] point at this cell's position
-// (its box row and column) in the staged record and scale boxes of plane m + 1 - k, the plane
-// the pull sources of the directions with c_m = k - 1 lie in (k = 1: this plane), so the source
-// of direction i sits at the compile-time offset -(c_i,b RX + c_i,a) from rec[1 + c_i,m].  The rest pair
-// (f_0^r, f_0^b) is the cell's own, read from global memory.  Output as pull_cell_dev: g_i =
-// (f_i, 0), the colour totals (sr, sb) summed rest pair first with Fast2Sum, and their rounding
-// errors (lr, lb): sr + lr is the exact sum of the split values.  A cell none of whose links
-// bounces back (sbits == 0, nearly every cell) takes a path whose addresses are all fixed
-// offsets; the others take the general one.
+// with the source's record as pull_cell_rc does.  rec / ref are the staged record and scale boxes
+// (flat shared arrays of RS x RY x RX); bx[k] is the flat index of this cell's box position in
+// plane m + 1 - k, the plane that the pull sources of the directions with c_m = k - 1 lie in
+// (k = 1: this plane), so the source of direction i sits at the compile-time offset
+// -(c_i,b RX + c_i,a) from bx[1 + c_i,m].  The rest pair (f_0^r, f_0^b) is the cell's own, read
+// from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb) summed
+// rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact sum of
+// the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
+// takes a path whose addresses are all fixed offsets; the others take the general one.
 template <int Q, int S, int RX>
 __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
                                                PlaneOffsets po, uint32_t sbits,
-                                               const float4* const (&rec)[3],
-                                               const float* const (&ref)[3], V2<float> (&g)[Q],
+                                               const float4* rec, const float* ref,
+                                               const int (&bx)[3], V2<float> (&g)[Q],
                                                float& sr, float& sb, float& lr, float& lb) {
   using L = Lattice<Q>;
   using H = typename Storage<S>::half_t;
-  using P = typename H::packed;
   const char* base = reinterpret_cast<const char*>(A.pin);
   const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
   const unsigned short* dev = reinterpret_cast<const unsigned short*>(base + lay.dev);
@@ -428,12 +427,10 @@ __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl
     g[0] = {acc.x + acc.y, 0.0f};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int off = -(L::cb(i) * RX + L::ca(i));
-      const float4 rc = rec[1 + L::cm(i)][off];
-      const float rf = ref[1 + L::cm(i)][off];
-      P pv;
-      *reinterpret_cast<unsigned short*>(&pv) = raw[i];
-      const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
+      const int e = bx[1 + L::cm(i)] - (L::cb(i) * RX + L::ca(i));
+      const float4 rc = rec[e];
+      const float rf = ref[e];
+      const float f = fmaf(H::unpack_bits(raw[i]), inv_scale, float(rc16_ratio<L>(i)) * rf);
       const float fr = rc_red<L>(i, rc.x, f, rc_cv<L>(i, rc));
       fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
       g[i] = {f, 0.0f};
@@ -455,12 +452,10 @@ __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl
     for (int i = 1; i < Q; ++i) {
       const bool bounce = (sbits >> i) & 1u;
       // the source's record and scale (the cell's own for a bounced link)
-      const int off = -(L::cb(i) * RX + L::ca(i));
-      const float4 rc = bounce ? rec[1][0] : rec[1 + L::cm(i)][off];
-      const float rf = bounce ? ref[1][0] : ref[1 + L::cm(i)][off];
-      P pv;
-      *reinterpret_cast<unsigned short*>(&pv) = raw[i];
-      const float f = fmaf(H::unpack(pv), inv_scale, float(rc16_ratio<L>(i)) * rf);
+      const int e = bounce ? bx[1] : bx[1 + L::cm(i)] - (L::cb(i) * RX + L::ca(i));
+      const float4 rc = rec[e];
+      const float rf = ref[e];
+      const float f = fmaf(H::unpack_bits(raw[i]), inv_scale, float(rc16_ratio<L>(i)) * rf);
       float cv = rc_cv<L>(i, rc);
       if (bounce) cv = -cv;
       const float fr = rc_red<L>(i, rc.x, f, cv);
@@ -1039,13 +1034,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
             pull_cell_dev<Q, S>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
                                 L::D3 ? hy + 1 : 0, ps, restbox, tmp, sr, sb, lr_unused, lb_unused);
           else if constexpr (RC16IN) {
-            const int ex = hx + 1, ey = L::D3 ? hy + 1 : 0;
-            const float4* const rp[3] = {&rec_ring[ps[0]][ey][ex], &rec_ring[ps[1]][ey][ex],
-                                         &rec_ring[ps[2]][ey][ex]};
-            const float* const fp[3] = {&ref_ring[ps[0]][ey][ex], &ref_ring[ps[1]][ey][ex],
-                                        &ref_ring[ps[2]][ey][ex]};
-            pull_cell_rc16<Q, S, RX>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, rp, fp, tmp, sr, sb,
-                                     lr_unused, lb_unused);
+            const int c0 = (L::D3 ? hy + 1 : 0) * RX + hx + 1;
+            const int bx[3] = {ps[0] * RY * RX + c0, ps[1] * RY * RX + c0, ps[2] * RY * RX + c0};
+            pull_cell_rc16<Q, S, RX>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, &rec_ring[0][0][0],
+                                     &ref_ring[0][0][0], bx, tmp, sr, sb, lr_unused, lb_unused);
           }
           else
             pull_cell_rc<Q>(A, hs, sidx(G, hs.a, hs.b, p.m), po, bits, hx + 1,
@@ -1072,13 +1064,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
                               L::D3 ? ly0 + c * TY + 2 : 0, ps, restbox, g[c], out[c].rr,
                               out[c].rb, out[c].lr, out[c].lb);
         else if constexpr (RC16IN) {
-          const int ex = lx + 2, ey = L::D3 ? ly0 + c * TY + 2 : 0;
-          const float4* const rp[3] = {&rec_ring[ps[0]][ey][ex], &rec_ring[ps[1]][ey][ex],
-                                       &rec_ring[ps[2]][ey][ex]};
-          const float* const fp[3] = {&ref_ring[ps[0]][ey][ex], &ref_ring[ps[1]][ey][ex],
-                                      &ref_ring[ps[2]][ey][ex]};
-          pull_cell_rc16<Q, S, RX>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, rp, fp, g[c],
-                                   out[c].rr, out[c].rb, out[c].lr, out[c].lb);
+          const int c0 = (L::D3 ? ly0 + c * TY + 2 : 0) * RX + lx + 2;
+          const int bx[3] = {ps[0] * RY * RX + c0, ps[1] * RY * RX + c0, ps[2] * RY * RX + c0};
+          pull_cell_rc16<Q, S, RX>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits,
+                                   &rec_ring[0][0][0], &ref_ring[0][0][0], bx, g[c], out[c].rr,
+                                   out[c].rb, out[c].lr, out[c].lb);
         }
         else if constexpr (RCIN)
           pull_cell_rc<Q>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, lx + 2,
