@@ -196,10 +196,37 @@ __device__ __forceinline__ void collide_adjoint(const Physics& ph, const R (&fcb
   }
 }
 
+// Asynchronous copy of `bytes` (8 or 16) from global to shared memory, and its completion for
+// the issuing thread (cp.async; the copies land while the thread goes on).
+template <int BYTES>
+__device__ __forceinline__ void async_copy(void* smem_dst, const void* gsrc) {
+  static_assert(BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Kernel A's per-cell tail (replaces StepEpilogue in step_tile): reads lambda^{n+1} at the cell,
-// writes lg (state layout) and the auxiliary planes.
+// writes lg (state layout) and the auxiliary planes.  lambda^{n+1} of a cell of plane m is
+// copied into this thread's shared-memory column `lam` (Q vec slots, stride NT) by prefetch(), at
+// the start of the iteration that collides plane m, so the copies overlap the pulls of plane
+// m + 1; cell() waits for them and reads them from shared memory.
 struct AdjointEpilogue {
   AdjointOut o;
+  unsigned char* lam;  // this thread's column: Q slots of sizeof(vec), stride nt slots
+  int nt;
+  template <int Q, int S>
+  __device__ __forceinline__ void prefetch(const StepArgs& A, int si) const {
+    using Vec = typename Storage<S>::vec;
+    const int ns = A.g.nstore;
+    const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);
+    Vec* col = reinterpret_cast<Vec*>(lam);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) async_copy<sizeof(Vec)>(col + (size_t)i * nt, lin + (size_t)i * ns + si);
+    async_commit();
+  }
   template <int Q, int S, class R>
   __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, int si, int /*nimg*/,
                                        const int (&)[3], const R (&g)[Q], R rr, R rb, R irho,
@@ -207,10 +234,11 @@ struct AdjointEpilogue {
                                        int&, R&) const {
     using Vec = typename Storage<S>::vec;
     const int ns = A.g.nstore;
-    const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);
     Vec* lout = reinterpret_cast<Vec*>(o.lam_g);
+    async_wait_all();  // this thread's copies of plane m (only it reads its column)
+    const Vec* col = reinterpret_cast<const Vec*>(lam);
     auto lam_at = [&](int i) -> V2<R> {
-      const Vec v = __ldg(lin + (size_t)i * ns + si);
+      const Vec v = col[(size_t)i * nt];
       return {v.x, v.y};
     };
     auto lg_out = [&](int i, V2<R> v2) {
@@ -237,7 +265,10 @@ __global__ void __launch_bounds__(TX* TY, (S == ST_F64 ? 256 : 384) / (TX * TY))
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   long long n = 0;
   double d = 0.0;
-  const AdjointEpilogue E{O};
+  using Vec = typename Storage<S>::vec;
+  // lambda columns after the tile's own shared memory: slot i of thread t at (i TX TY + t)
+  const AdjointEpilogue E{O, dyn_smem + TileSmem<Q, S, TX, TY, 1>::BYTES + threadIdx.x * sizeof(Vec),
+                          TX * TY};
   step_tile<Q, S, TX, TY, 1, AdjointEpilogue>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d,
                                               threadIdx.x, -1, E);
 }

@@ -9,7 +9,9 @@ namespace {
 
 template <int Q, int S, int TX, int TY>
 KernelRef adj_ref() {
-  constexpr int smem = TileSmem<Q, S, TX, TY, 1>::BYTES;
+  // the tile's shared memory, then the prefetched lambda^{n+1} columns (Q vec per thread)
+  constexpr int smem = TileSmem<Q, S, TX, TY, 1>::BYTES +
+                       Q * TX * TY * (int)sizeof(typename Storage<S>::vec);
   const void* fn = (const void*)cg_adjoint_local_kernel<Q, S, TX, TY>;
   static bool attr = false;
   if (!attr) {

@@ -765,6 +765,11 @@ __device__ __forceinline__ int image_deltas(const Geom& g, int a, int b, int (&d
 // keeps each f_i), rho_r, rho_b and the neighbour phase field rnb are at hand: Eq.
 // (collision) to Eq. (recolor) and the store, the site byte of this step and the ledger terms.
 struct StepEpilogue {
+  // Called for each own fluid cell of plane m (storage index si) at the start of the iteration
+  // that collides plane m, before the pulls of plane m + 1: an epilogue that reads per-cell data
+  // of plane m can start fetching it here (the step itself reads nothing more).
+  template <int Q, int S>
+  __device__ __forceinline__ void prefetch(const StepArgs&, int /*si*/) const {}
   // (lr, lb): the rounding errors of rr, rb (16-bit storages: rr + lr is the exact mass)
   template <int Q, int S, class R>
   __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
@@ -1130,6 +1135,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       __syncthreads();
       continue;
     }
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (active[c] && cur[c].ok) epi.template prefetch<Q, S>(A, sidx(G, me[c].a, me[c].b, m));
     V2<R> g[CPT][Q];
     fill_plane(m + 1, nxt, g);
     __syncthreads();
