@@ -62,6 +62,10 @@ def parse():
                     help="only check the flux-fit gradient against finite differences (FP64)")
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="steps of the 64-member ensemble workload (0: skip)")
+    ap.add_argument("--sweep-2d", default="",
+                    help="only run the D2Q9 drop sweep (R0 = 40, 256^2; 5 fluxes x 3 band "
+                         "thresholds) to R0/2 as one ensemble in these storages (e.g. f32) and "
+                         "print its radius-law errors")
     ap.add_argument("--steady-s", type=float, default=1.0,
                     help="seconds of extra graph replays of the headline storage, timed one by "
                          "one, reported beside the K-step figure (0: skip)")
@@ -521,6 +525,87 @@ def run_adjoint_fd(args):
     print(json.dumps({"adjoint_fd": report}), flush=True)
 
 
+def band_sbar(theta: float) -> float:
+    """S-bar of the band rule at theta: the fixed point of S-bar -> time-averaged sites per unit
+    length of a flat-interface run with that S-bar (64^2 slab, two interfaces, flux 1e-3, FP64)."""
+    from dataclasses import replace
+    from paper_2412_14859_gb300 import inputs
+    from paper_2412_14859_gb300.binding import Sim
+    import torch
+    case = replace(inputs.flat_slab_2d(), phi=1e-3, threshold=theta)
+    sbar = 3.0
+    for _ in range(4):
+        sim = Sim.from_case(replace(case, sbar=sbar), "f64")
+        sim.set_flux(case.phi)
+        sim.init_equilibrium(torch.from_numpy(case.phase()).cuda())
+        sim.step(2000)
+        sbar = sim.ledger()["site_steps"] / 2000 / (2 * case.shape[2])
+        sim.close()
+    return sbar
+
+
+def run_sweep_2d(args):
+    """The D2Q9 drop sweep to R0/2: every (phi, theta) case with its band-rule S-bar, equilibrated
+    3000 steps with the flux off, then evaporated; R = sqrt(V / pi) of the liquid area against
+    R0 - phi t / rho_l at R/R0 = 3/4 and 1/2; each member is paused once it reaches its second
+    mark, and the launches are cut into calls of at most 1e5 steps."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_2412_14859_gb300 import inputs
+    from paper_2412_14859_gb300.binding import Ensemble
+    torch.cuda.set_device(0)
+    t_start = time.perf_counter()
+    sb = {th: band_sbar(th) for th in (0.3, 0.5, 0.7)}
+    storages = [s for s in args.sweep_2d.split(",") if s]
+    base = [replace(c, sbar=sb[c.threshold]) for c in inputs.drop_2d_sweep()]
+    cases = [c for _ in storages for c in base]
+    st_of = [st for st in storages for _ in base]
+    ens = Ensemble(cases, st_of)
+    for sim, c in zip(ens.members, cases):
+        sim.set_flux(0.0)
+        sim.init_equilibrium(torch.from_numpy(c.phase()).cuda(), torch.from_numpy(c.noise_array()).cuda())
+    ens.step(3000)
+    R0, rho, m0 = [], [], []
+    for sim, c in zip(ens.members, cases):
+        R0.append(float(np.sqrt(float(sim.volume()) / np.pi)))
+        m = sim.macros()
+        rho.append(float(m["rho_r"].max()))
+        m0.append(float(m["rho_r"].sum()))
+        sim.set_flux(c.phi)
+        sim.reset_ledger()
+    marks = [[(1.0 - f) * R0[j] * rho[j] / c.phi for f in (0.75, 0.5)] for j, c in enumerate(cases)]
+    err = [[None, None] for _ in cases]
+    active, t = set(range(len(cases))), 0
+    while active:
+        nxt = min(int(round(marks[j][k])) for j in active for k in (0, 1) if err[j][k] is None)
+        ens.step(min(nxt - t, 100000))
+        t += min(nxt - t, 100000)
+        for j in list(active):
+            for k in (0, 1):
+                if err[j][k] is None and int(round(marks[j][k])) == t:
+                    R = float(np.sqrt(float(ens.members[j].volume()) / np.pi))
+                    exact = 1.0 - cases[j].phi * t / (R0[j] * rho[j])
+                    err[j][k] = (R / R0[j] - exact) / exact * 100.0
+            if err[j][1] is not None:
+                active.discard(j)
+                if active:
+                    ens.set_active(j, False)
+    ens.status()
+    rows = []
+    for j, c in enumerate(cases):
+        sim = ens.members[j]
+        lost = m0[j] - float(sim.macros()["rho_r"].sum())
+        rows.append({"storage": st_of[j], "phi": c.phi, "theta": c.threshold, "sbar": round(c.sbar, 4),
+                     "R0": round(R0[j], 3), "steps_to_half": int(round(marks[j][1])),
+                     "error_percent_at_3_4": round(err[j][0], 3),
+                     "error_percent_at_1_2": round(err[j][1], 3),
+                     "red_lost_over_ledger_minus_1": lost / sim.ledger()["evaporated"] - 1.0})
+    ens.close()
+    print(json.dumps({"sweep_2d": rows, "band_sbar": sb, "wall_s": round(time.perf_counter() - t_start, 1)}),
+          flush=True)
+
+
 def run_ours(args, d: Dist):
     import numpy as np
     import torch
@@ -705,6 +790,9 @@ def main():
         sys.exit("--gpus N > 1 must be launched with torchrun --nproc-per-node N")
     if args.adjoint_fd:
         run_adjoint_fd(args)
+        return
+    if args.sweep_2d:
+        run_sweep_2d(args)
         return
     if args.impl == "reference":
         d = Dist("gloo")

@@ -33,6 +33,29 @@ def sphere_radius(sim, n):
     return float(np.mean(out))
 
 
+def radius_definitions(sim, n, max0, V0, R0h, R0i):
+    """The drop radius three ways, each relative to its own value at the start of evaporation:
+    half of the current maximum of rho_r (the paper's definition, as sphere_radius), half of the
+    maximum at the start, and the volume-equivalent (3 V / 4 pi)^(1/3), V = sum (1 + rho^N) / 2."""
+    rr = sim.macros()["rho_r"].cpu().numpy()
+    lo, hi = n // 2 - 1, n // 2 + 1
+    profiles = [rr[lo:hi, lo:hi, :].mean(axis=(0, 1)), rr[lo:hi, :, lo:hi].mean(axis=(0, 2)),
+                rr[:, lo:hi, lo:hi].mean(axis=(1, 2))]
+
+    def crossing(level):
+        out = []
+        for prof in profiles:
+            for idx in (np.arange(n // 2, n), np.arange(n // 2 - 1, -1, -1)):
+                p = prof[idx]
+                j = int(np.argmax(p < level))
+                out.append((j - 1) + (p[j - 1] - level) / (p[j - 1] - p[j]) + 0.5)
+        return float(np.mean(out))
+
+    return {"half_current_max": crossing(0.5 * rr.max()) / R0h,
+            "half_initial_max": crossing(0.5 * max0) / R0i,
+            "volume_equivalent": (float(sim.volume()) / V0) ** (1.0 / 3.0)}
+
+
 @pytest.mark.parametrize("case", GOLDEN["cases"], ids=lambda c: f"phi{c['phi']}")
 def test_evaporating_sphere_matches_paper_accuracy(case):
     n = 128
@@ -45,6 +68,8 @@ def test_evaporating_sphere_matches_paper_accuracy(case):
     R0 = sphere_radius(sim, n)
     rho0 = float(sim.macros()["rho_r"].max())
     assert R0 == pytest.approx(44.0, abs=0.5)
+    V0 = float(sim.volume())
+    R0i = radius_definitions(sim, n, rho0, V0, 1.0, 1.0)["half_initial_max"]
     te = R0 * rho0 / case["phi"]
     sim.set_flux(case["phi"])
     t = 0
@@ -55,12 +80,17 @@ def test_evaporating_sphere_matches_paper_accuracy(case):
         t += k
         exact = 1.0 - t / te
         errs.append(abs(sphere_radius(sim, n) / R0 - exact) / exact * 100.0)
+        defs = radius_definitions(sim, n, rho0, V0, R0, R0i)
+        print("phi", case["phi"], "t*", ts, "signed errors % by definition",
+              {k2: round((v - exact) / exact * 100.0, 2) for k2, v in defs.items()})
     # the paper: 0.2 % and 2.1 % at phi = 0.03, 0.5 % and 0.4 % at phi = 3e-4 (about 3 % against
-    # the variable-density law); here within the same scale: well under 1 % while R/R0 > 0.4, a
-    # few percent near R/R0 = 0.2
+    # the variable-density law).  Measured: 0.06 % and 3.3 % at phi = 0.03, 0.28 % and 1.9 % at
+    # phi = 3e-4.  Late (R about 8.4, two interface widths) the radius depends on its definition
+    # by several points on the same run at phi = 3e-4: half of the current maximum 1.9 %, half of
+    # the initial maximum 3.0 %, volume-equivalent 4.3 %; the maximum of rho_r has risen 5 %
     print("sphere phi", case["phi"], "errors %", [round(e, 2) for e in errs])
     assert errs[0] <= 0.5, errs
-    assert errs[1] <= 5.0, errs
+    assert errs[1] <= {0.03: 3.8, 0.0003: 2.4}[case["phi"]], errs
 
 
 def drop_radius_2d(sim, n):
@@ -263,6 +293,8 @@ def test_density_contrast_sphere_with_outlets(case):
     sim.set_outlets(1.0, 1.0)
     sim.set_flux(phi)
     late = gamma == 4.0 and phi == 0.003
+    V0 = float(sim.volume())
+    R0i = radius_definitions(sim, n, rho0, V0, 1.0, 1.0)["half_initial_max"]
     t = 0
     for ts in (0.5, 0.6, 0.7, 0.8, 0.85):
         k = int(round(ts * te)) - t
@@ -270,8 +302,17 @@ def test_density_contrast_sphere_with_outlets(case):
         t += k
         exact = 1.0 - t / te
         err = abs(sphere_radius(sim, n) / R0 - exact) / exact * 100.0
+        defs = radius_definitions(sim, n, rho0, V0, R0, R0i)
+        print("gamma", gamma, "phi", phi, "t*", ts, "signed errors % by definition",
+              {k2: round((v - exact) / exact * 100.0, 2) for k2, v in defs.items()})
         if late and ts > 0.7:
-            assert err <= 15.0, (ts, err)
+            # R < 9 here, about two interface widths: the half-maximum crossing follows the
+            # profile of a drop whose maximum has risen 7 % (measured 6.0 % and 11.8 %); the
+            # volume-equivalent radius (3V / 4 pi)^(1/3) of the same run stays inside the range
+            # the paper prints (measured 4.4 % and 3.5 %)
+            assert err <= {0.8: 6.5, 0.85: 12.5}[ts], (ts, err)
+            err_v = abs((float(sim.volume()) / V0) ** (1.0 / 3.0) - exact) / exact * 100.0
+            assert err_v <= case["error_percent_range"][1] + 0.4, (ts, err_v)
         else:
             assert err <= case["error_percent_range"][1], (ts, err)
     sim.close()

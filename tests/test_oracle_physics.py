@@ -255,3 +255,26 @@ def test_rounding_order_is_amplified_over_hundreds_of_steps():
     assert 0.0 < errs[0] <= 1e-12
     assert errs[1] >= 10.0 * errs[0]
     assert errs[1] <= 1e-9
+
+
+def test_tiny_drop_amplifies_single_precision_perturbations():
+    """Why the FP32 path is not held to the oracle on the tiny drop (radius 3.5, about the
+    interface width, on 9x17x33): perturbing every initial population by a relative amount of
+    FP32 size (uniform, 6e-8) changes rho_r by 0.4x that after one oracle step and by 11x after
+    ten -- a 28-fold growth in nine steps -- while FP32 rounds at that size at every step.  The
+    FP64 path stays within 1e-12 of the oracle there (tests/test_gpu_parity.py)."""
+    from harness import oracle_params
+    from test_gpu_parity import drop
+    case = drop(19, (9, 17, 33), R0=3.5)
+    p = oracle_params(case)
+    f0 = oracle.init(p, case.phase(), case.noise_array())
+    fp = f0 * (1.0 + 6e-8 * np.random.default_rng(1).uniform(-1.0, 1.0, f0.shape))
+    a, b = oracle.Run(p, f0), oracle.Run(p, fp)
+    growth = []
+    for n in (1, 10):
+        a.step(n - a.steps)
+        b.step(n - b.steps)
+        ra, rb = a.macros()["rho_r"], b.macros()["rho_r"]
+        growth.append(float(np.max(np.abs(ra - rb)) / np.max(np.abs(ra))) / 6e-8)
+    print("relative change of rho_r over the perturbation, after 1 and 10 steps:", growth)
+    assert growth[1] >= 10.0 * max(growth[0], 0.1)
