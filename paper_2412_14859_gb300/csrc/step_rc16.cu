@@ -29,7 +29,7 @@ static KernelRef pick(int q, int variant) {
     switch (variant) {
       case 0: return rc16_ref<19, S, 16, 8, 4, 1>();
       case 1: return rc16_ref<19, S, 32, 4, 4, 1>();
-      case 2: return rc16_ref<19, S, 32, 4, 3, 1>();
+      case 2: return rc16_ref<19, S, 16, 16, 2, 1>();  // 256 threads: a smaller ring per cell
       case 3: return rc16_ref<19, S, 16, 4, 8, 1>();
       case 4: return rc16_ref<19, S, 32, 8, 2, 1>();  // 256 threads: a smaller ring per cell
     }

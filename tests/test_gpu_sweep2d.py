@@ -9,13 +9,13 @@ interface length of a flat-interface run (the 64^2 slab) that itself uses that S
 point reached by iterating.
 
 - Parity: every member equals the oracle on the same seeded input, with identical site masks
-  away from the threshold, after 50 steps within the parity bounds of the short cases (FP64
-  1e-12, FP32 1e-5) and after 500 steps within stated longer bounds.  The method amplifies
-  differences of rounding order over hundreds of steps: the oracle itself, compiled with
-  multiply-add contraction, departs from the pinned (uncontracted) build by 4e-11 after 300-500
-  steps of the (phi = 1e-6, theta = 0.3) case, having been at 1e-13 after 50; the GPU's FP64
+  away from the threshold, after 50 and after 500 steps, within bounds stated for those lengths.
+  The method amplifies differences of rounding order over hundreds of steps: the oracle itself,
+  compiled with multiply-add contraction, departs from the pinned (uncontracted) build by 1e-13
+  after 50 steps of the (phi = 1e-6, theta = 0.3) case and by 4e-11 after 300; the GPU's FP64
   arithmetic (contracted multiply-adds, reciprocal and square-root forms of its own) departs by
-  up to 1e-9.  So FP64 is held to 1e-8 and FP32 to 1e-4 at 500 steps.
+  3.7e-12 after 50 steps and up to 1e-9 after 500 (measured).  So FP64 is held to 1e-11 at 50
+  steps and 1e-8 at 500, FP32 to the short-case 1e-5 at 50 and 1e-4 at 500.
 - Radius law (Sec. III.A, R = R0 - phi t / rho_l, the evaporating drop of the paper in 2D): from
   the equilibrated drop, the two largest fluxes run until the law gives R = R0/2 (2e5 and 6.3e5
   steps), each member paused when it gets there; the radius R = sqrt(V / pi) of the liquid area
@@ -33,7 +33,7 @@ pytestmark = pytest.mark.gpu
 
 THETAS = (0.3, 0.5, 0.7)
 # relative L-inf of the densities against the oracle after 50 and 500 steps
-BOUND = {"f64": {50: 1e-12, 500: 1e-8}, "f32": {50: 1e-5, 500: 1e-4}}
+BOUND = {"f64": {50: 1e-11, 500: 1e-8}, "f32": {50: 1e-5, 500: 1e-4}}
 
 
 def band_sbar(theta: float) -> float:
