@@ -821,7 +821,11 @@ struct TileSmem {
 // planes of the chunk: the loop runs that many barrier rounds (the extra ones idle), so several
 // tiles with different chunk lengths can share one CTA's barriers.  epi: the per-cell tail
 // (StepEpilogue for the step itself; the adjoint passes its own).
-template <int Q, int S, int TX, int TY, int CPT, class Epi = StepEpilogue>
+// PF (storages that pull pairs from global memory without staging): the own cells' pulls of the
+// next plane are issued one fill ahead, into registers, so their loads are in flight during the
+// rest of that fill, the barrier and the collision of the current plane instead of being waited
+// for at once (the same values, loaded earlier; more registers live across the collision).
+template <int Q, int S, int TX, int TY, int CPT, class Epi = StepEpilogue, bool PF = false>
 __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk, unsigned char* smem,
                                           long long& n_sites, double& removed,
                                           int tid = threadIdx.x, int iters = -1,
@@ -1012,6 +1016,25 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 
   // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
   // post-exchange populations are returned in g.
+  static_assert(!(PF && STAGE), "pulls issued ahead only for storages without staged sources");
+  V2<R> pf[CPT][Q];   // PF: the own cells' pulled populations of the next plane to fill
+  uint32_t pfbits[CPT];
+  bool pfok[CPT];
+  auto issue = [&](int um) {  // PF: issue the own cells' pulls of plane um
+    if constexpr (PF) {
+      const Plane p = make_plane(G, um);
+      const PlaneOffsets po = plane_offsets(G, p.m);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int cl = (p.m * G.nb + me[c].b) * G.na + me[c].a;
+        uint32_t bits = 0;
+        pfok[c] = solid_bits<L>(G, me[c], p, cl, bits);
+        pfbits[c] = bits;
+        if (pfok[c]) pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf[c]);
+      }
+    }
+  };
+  (void)issue;
   auto fill_plane = [&](int um, CellScalars(&out)[CPT], V2<R>(&g)[CPT][Q]) {
     const Plane p = make_plane(G, um);
     const PlaneOffsets po = plane_offsets(G, p.m);
@@ -1059,6 +1082,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {  // issue every load of every own cell first
       cells[c] = (p.m * G.nb + me[c].b) * G.na + me[c].a;
+      if constexpr (PF) {  // issued one fill ahead
+        out[c].ok = pfok[c];
+        out[c].bits = pfbits[c];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[c][i] = pf[c][i];
+        continue;
+      }
       uint32_t bits = 0;
       out[c].ok = solid_bits<L>(G, me[c], p, cells[c], bits);
       out[c].bits = bits;
@@ -1082,6 +1112,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
           pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, g[c]);
       }
     }
+    issue(um + 1);  // PF: the next fill's own pulls, in flight from here
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       R rn = R(0);
@@ -1108,6 +1139,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       stage_rest(um + 2);
   };
 
+  issue(m0 - 1);  // PF: the first fill's own pulls
   stage_rest(m0 - 2);
   stage_rest(m0 - 1);
   stage_rest(m0);
@@ -1255,12 +1287,12 @@ __device__ __forceinline__ void ledger_fold(const Reduce& red, long long n, doub
   }
 }
 
-template <int Q, int S, int TX, int TY, int MINB, int CPT>
+template <int Q, int S, int TX, int TY, int MINB, int CPT, bool PF = false>
 __global__ void __launch_bounds__(TX* TY, MINB) cg_step_kernel(const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   long long n = 0;
   double d = 0.0;
-  step_tile<Q, S, TX, TY, CPT>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d);
+  step_tile<Q, S, TX, TY, CPT, StepEpilogue, PF>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d);
   block_sum<TX * TY>(n, d);
   ledger_fold(A.red, n, d);
 }
