@@ -399,41 +399,24 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
 // rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact sum of
 // the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
 // takes a path whose addresses are all fixed offsets; the others take the general one.
-template <int Q, int S, int RX>
-__device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
-                                               PlaneOffsets po, uint32_t sbits,
-                                               const float4* rec, const float* ref,
-                                               const int (&bx)[3], V2<float> (&g)[Q],
-                                               float& sr, float& sb, float& lr, float& lb) {
+// The global loads of pull_cell_rc16: the 16-bit values of the cell's pulled moving populations
+// (raw[i], i >= 1) and its own rest pair r0; they need nothing staged, so they can be issued
+// ahead of the decode.
+template <int Q, int S>
+__device__ __forceinline__ void rc16_load(const StepArgs& A, const Slot& sl, int si, PlaneOffsets po,
+                                          uint32_t sbits, unsigned short (&raw)[Q], float2& r0) {
   using L = Lattice<Q>;
-  using H = typename Storage<S>::half_t;
   const char* base = reinterpret_cast<const char*>(A.pin);
   const Rc16Layout lay = rc16_layout(Q, A.g.nstore);
   const unsigned short* dev = reinterpret_cast<const unsigned short*>(base + lay.dev);
   const int ns = A.g.nstore;
-  unsigned short raw[Q];
-  const float inv_scale = A.ph.inv_scale;
-  float2 acc, lo = make_float2(0.0f, 0.0f);
   if (sbits == 0) {
-    // all deviation loads first
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int src = si + (L::ca(i) > 0 ? sl.dxm : (L::ca(i) < 0 ? sl.dxp : 0)) +
                       (L::cb(i) > 0 ? sl.dym : (L::cb(i) < 0 ? sl.dyp : 0)) +
                       (L::cm(i) > 0 ? po.dm_lo : (L::cm(i) < 0 ? po.dm_hi : 0));
       raw[i] = __ldg(dev + (i - 1) * ns + src);
-    }
-    acc = __ldg(reinterpret_cast<const float2*>(base) + si);
-    g[0] = {acc.x + acc.y, 0.0f};
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int e = bx[1 + L::cm(i)] - (L::cb(i) * RX + L::ca(i));
-      const float4 rc = rec[e];
-      const float rf = ref[e];
-      const float f = fmaf(H::unpack_bits(raw[i]), inv_scale, float(rc16_ratio<L>(i)) * rf);
-      const float fr = rc_red<L>(i, rc.x, f, rc_cv<L>(i, rc));
-      fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
-      g[i] = {f, 0.0f};
     }
   } else {
 #pragma unroll
@@ -446,8 +429,34 @@ __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl
       const int dir = bounce ? opp(i) : i;
       raw[i] = __ldg(dev + (size_t)(dir - 1) * ns + src);
     }
-    acc = __ldg(reinterpret_cast<const float2*>(base) + si);
-    g[0] = {acc.x + acc.y, 0.0f};
+  }
+  r0 = __ldg(reinterpret_cast<const float2*>(base) + si);
+}
+
+// The arithmetic of pull_cell_rc16 on loaded values (see there).
+template <int Q, int S, int RX>
+__device__ __forceinline__ void rc16_decode(const StepArgs& A, uint32_t sbits,
+                                            const unsigned short (&raw)[Q], float2 r0,
+                                            const float4* rec, const float* ref, const int (&bx)[3],
+                                            V2<float> (&g)[Q], float& sr, float& sb, float& lr,
+                                            float& lb) {
+  using L = Lattice<Q>;
+  using H = typename Storage<S>::half_t;
+  const float inv_scale = A.ph.inv_scale;
+  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
+  g[0] = {r0.x + r0.y, 0.0f};
+  if (sbits == 0) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int e = bx[1 + L::cm(i)] - (L::cb(i) * RX + L::ca(i));
+      const float4 rc = rec[e];
+      const float rf = ref[e];
+      const float f = fmaf(H::unpack_bits(raw[i]), inv_scale, float(rc16_ratio<L>(i)) * rf);
+      const float fr = rc_red<L>(i, rc.x, f, rc_cv<L>(i, rc));
+      fast_two_sum_acc(acc, lo, make_float2(fr, f - fr));
+      g[i] = {f, 0.0f};
+    }
+  } else {
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const bool bounce = (sbits >> i) & 1u;
@@ -467,6 +476,29 @@ __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl
   sb = acc.y;
   lr = lo.x;
   lb = lo.y;
+}
+
+// 16-bit recolour-on-pull layout: pull one cell.  Each moving population is decoded from its
+// 16-bit deviation and the source's rest-state scale Rf, f_i = fl(r_i Rf + dev / s), and split
+// with the source's record as pull_cell_rc does.  rec / ref are the staged record and scale boxes
+// (flat shared arrays of RS x RY x RX); bx[k] is the flat index of this cell's box position in
+// plane m + 1 - k, the plane that the pull sources of the directions with c_m = k - 1 lie in
+// (k = 1: this plane), so the source of direction i sits at the compile-time offset
+// -(c_i,b RX + c_i,a) from bx[1 + c_i,m].  The rest pair (f_0^r, f_0^b) is the cell's own, read
+// from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb) summed
+// rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact sum of
+// the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
+// takes a path whose addresses are all fixed offsets; the others take the general one.
+template <int Q, int S, int RX>
+__device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
+                                               PlaneOffsets po, uint32_t sbits,
+                                               const float4* rec, const float* ref,
+                                               const int (&bx)[3], V2<float> (&g)[Q],
+                                               float& sr, float& sb, float& lr, float& lb) {
+  unsigned short raw[Q];
+  float2 r0;
+  rc16_load<Q, S>(A, sl, si, po, sbits, raw, r0);
+  rc16_decode<Q, S, RX>(A, sbits, raw, r0, rec, ref, bx, g, sr, sb, lr, lb);
 }
 
 template <class R>
@@ -1016,10 +1048,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 
   // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
   // post-exchange populations are returned in g.
-  static_assert(!(PF && STAGE), "pulls issued ahead only for storages without staged sources");
+  // PF with the 16-bit recolour-on-pull layout: only the global loads (the 16-bit values and the
+  // rest pair) are issued ahead; the decode needs the staged records of its fill
+  static_assert(!(PF && STAGE && !RC16IN), "pulls issued ahead: pairs or 16-bit recolour on pull");
   V2<R> pf[CPT][Q];   // PF: the own cells' pulled populations of the next plane to fill
+  unsigned short pf16[CPT][Q];  // PF, 16-bit recolour on pull: their raw values
+  float2 pf16r0[CPT];
   uint32_t pfbits[CPT];
   bool pfok[CPT];
+  (void)pf;
+  (void)pf16;
+  (void)pf16r0;
   auto issue = [&](int um) {  // PF: issue the own cells' pulls of plane um
     if constexpr (PF) {
       const Plane p = make_plane(G, um);
@@ -1030,7 +1069,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         uint32_t bits = 0;
         pfok[c] = solid_bits<L>(G, me[c], p, cl, bits);
         pfbits[c] = bits;
-        if (pfok[c]) pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf[c]);
+        if (pfok[c]) {
+          if constexpr (RC16IN)
+            rc16_load<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf16[c], pf16r0[c]);
+          else
+            pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf[c]);
+        }
       }
     }
   };
@@ -1085,8 +1129,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       if constexpr (PF) {  // issued one fill ahead
         out[c].ok = pfok[c];
         out[c].bits = pfbits[c];
+        if constexpr (RC16IN) {
+          if (out[c].ok) {
+            const int c0 = (L::D3 ? ly0 + c * TY + 2 : 0) * RX + lx + 2;
+            const int bx[3] = {ps[0] * RY * RX + c0, ps[1] * RY * RX + c0, ps[2] * RY * RX + c0};
+            rc16_decode<Q, S, RX>(A, pfbits[c], pf16[c], pf16r0[c], &rec_ring[0][0][0],
+                                  &ref_ring[0][0][0], bx, g[c], out[c].rr, out[c].rb, out[c].lr,
+                                  out[c].lb);
+          }
+        } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[c][i] = pf[c][i];
+          for (int i = 0; i < Q; ++i) g[c][i] = pf[c][i];
+        }
         continue;
       }
       uint32_t bits = 0;
