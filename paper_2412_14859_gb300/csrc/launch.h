@@ -11,8 +11,8 @@ namespace cgevap {
 struct TileCfg {
   int tx, ty;
 };
-constexpr int kNumTiles3D = 7;  // variants 5, 6: storages that have them (others repeat 0, 1)
-constexpr TileCfg kTiles3D[kNumTiles3D] = {{32, 4}, {16, 8}, {16, 16}, {16, 4}, {32, 8}, {16, 8}, {16, 8}};
+constexpr int kNumTiles3D = 5;
+constexpr TileCfg kTiles3D[kNumTiles3D] = {{32, 4}, {16, 8}, {16, 16}, {16, 4}, {32, 8}};
 constexpr int kNumTiles2D = 2;
 constexpr TileCfg kTiles2D[kNumTiles2D] = {{128, 1}, {64, 1}};
 

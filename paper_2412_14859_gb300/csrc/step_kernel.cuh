@@ -400,8 +400,7 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
 // the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
 // takes a path whose addresses are all fixed offsets; the others take the general one.
 // The global loads of pull_cell_rc16: the 16-bit values of the cell's pulled moving populations
-// (raw[i], i >= 1) and its own rest pair r0; they need nothing staged, so they can be issued
-// ahead of the decode.
+// (raw[i], i >= 1) and its own rest pair r0 (they need nothing staged).
 template <int Q, int S>
 __device__ __forceinline__ void rc16_load(const StepArgs& A, const Slot& sl, int si, PlaneOffsets po,
                                           uint32_t sbits, unsigned short (&raw)[Q], float2& r0) {
@@ -1048,17 +1047,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
 
   // Pull plane um for the own cells and the ring cell; write rho^N to the ring; the own cells'
   // post-exchange populations are returned in g.
-  // PF with the 16-bit recolour-on-pull layout: only the global loads (the 16-bit values and the
-  // rest pair) are issued ahead; the decode needs the staged records of its fill
-  static_assert(!(PF && STAGE && !RC16IN), "pulls issued ahead: pairs or 16-bit recolour on pull");
+  // PF: the own cells' pulls issued one fill ahead (storages whose pulls need nothing staged; the
+  // 16-bit ones are bound by their instruction count, not by load latency, and gain nothing)
+  static_assert(!(PF && STAGE), "pulls issued ahead only for storages without staged sources");
   V2<R> pf[CPT][Q];   // PF: the own cells' pulled populations of the next plane to fill
-  unsigned short pf16[CPT][Q];  // PF, 16-bit recolour on pull: their raw values
-  float2 pf16r0[CPT];
   uint32_t pfbits[CPT];
   bool pfok[CPT];
   (void)pf;
-  (void)pf16;
-  (void)pf16r0;
   auto issue = [&](int um) {  // PF: issue the own cells' pulls of plane um
     if constexpr (PF) {
       const Plane p = make_plane(G, um);
@@ -1069,12 +1064,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         uint32_t bits = 0;
         pfok[c] = solid_bits<L>(G, me[c], p, cl, bits);
         pfbits[c] = bits;
-        if (pfok[c]) {
-          if constexpr (RC16IN)
-            rc16_load<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf16[c], pf16r0[c]);
-          else
-            pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf[c]);
-        }
+        if (pfok[c]) pull_cell<Q, S>(A, me[c], sidx(G, me[c].a, me[c].b, p.m), po, bits, pf[c]);
       }
     }
   };
@@ -1129,18 +1119,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       if constexpr (PF) {  // issued one fill ahead
         out[c].ok = pfok[c];
         out[c].bits = pfbits[c];
-        if constexpr (RC16IN) {
-          if (out[c].ok) {
-            const int c0 = (L::D3 ? ly0 + c * TY + 2 : 0) * RX + lx + 2;
-            const int bx[3] = {ps[0] * RY * RX + c0, ps[1] * RY * RX + c0, ps[2] * RY * RX + c0};
-            rc16_decode<Q, S, RX>(A, pfbits[c], pf16[c], pf16r0[c], &rec_ring[0][0][0],
-                                  &ref_ring[0][0][0], bx, g[c], out[c].rr, out[c].rb, out[c].lr,
-                                  out[c].lb);
-          }
-        } else {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) g[c][i] = pf[c][i];
-        }
+        for (int i = 0; i < Q; ++i) g[c][i] = pf[c][i];
         continue;
       }
       uint32_t bits = 0;

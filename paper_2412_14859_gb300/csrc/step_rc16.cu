@@ -6,12 +6,10 @@
 
 namespace cgevap {
 
-// PF: the 16-bit values and rest pairs of the next plane's own cells loaded one fill ahead
-// (pairs-in kernels read FP32 pairs, without staging, and take the pairs' PF)
-template <int Q, int S, int TX, int TY, int MINB, int CPT, bool PF = false>
+template <int Q, int S, int TX, int TY, int MINB, int CPT>
 static KernelRef rc16_ref() {
   constexpr int smem = TileSmem<Q, S, TX, TY, CPT>::BYTES;
-  const void* fn = (const void*)cg_step_kernel<Q, S, TX, TY, MINB, CPT, PF>;
+  const void* fn = (const void*)cg_step_kernel<Q, S, TX, TY, MINB, CPT>;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
@@ -34,8 +32,6 @@ static KernelRef pick(int q, int variant) {
       case 2: return rc16_ref<19, S, 16, 16, 2, 1>();  // 256 threads: a smaller ring per cell
       case 3: return rc16_ref<19, S, 16, 4, 8, 1>();
       case 4: return rc16_ref<19, S, 32, 8, 2, 1>();  // 256 threads: a smaller ring per cell
-      case 5: return rc16_ref<19, S, 16, 8, 4, 1, true>();
-      case 6: return rc16_ref<19, S, 16, 8, 3, 1, true>();
     }
   } else if (q == 9) {
     switch (variant) {

@@ -49,7 +49,7 @@ def test_step_matches_oracle(name, case, steps, storage):
 
 
 @pytest.mark.parametrize("storage", ["f16rc", "bf16rc"])
-@pytest.mark.parametrize("q,shape,nvar", [(9, (1, 40, 130), 2), (19, (12, 21, 37), 7)])
+@pytest.mark.parametrize("q,shape,nvar", [(9, (1, 40, 130), 2), (19, (12, 21, 37), 5)])
 def test_every_variant_matches_oracle(storage, q, shape, nvar):
     case = inputs.Case("variants", q, shape, R0=5.0, noise=1e-6, phi=1e-5, rho_r_in=2.0)
     run = oracle_run(case, 6)
