@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=192)
-    ap.add_argument("--storages", default="f32,f16rc,bf16rc,f32rc,f16dev,bf16dev,f64")
+    ap.add_argument("--storages", default="f32,f32x,f16rc,bf16rc,f32rc,f16dev,bf16dev,f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")

@@ -89,6 +89,14 @@ extern "C" {
                              2 (28 + 2 (Q - 1)) + 1 bytes per lattice update (129 for D3Q19).
                              An imported state is held as FP32 pairs until the next step. */
 #define CGEVAP_BF16RC 6   /* as F16RC with BF16 values (s = 1)                                */
+#define CGEVAP_F32X 7     /* the FP32 pairs of CGEVAP_F32 with each colour's mass carried
+                             exactly through the step: the pulled pairs are summed per colour
+                             without rounding error, the exchange's rounding is kept, and the
+                             rest pair is stored as the exact post-exchange colour masses less
+                             the stored moving pairs.  Same layout and bytes as F32; at small
+                             fluxes F32 removes less red mass than the ledger records (the
+                             exchange's phi / S-bar is rounded against rest populations of
+                             order 0.1 - 1 at every site and step), F32X does not. */
 
 /* ---- element types of caller buffers ---- */
 #define CGEVAP_DTYPE_F64 0
@@ -106,7 +114,7 @@ typedef struct cgevap_params {
   int site_rule;          /* CGEVAP_SITES_GRADIENT, CGEVAP_SITES_BAND or CGEVAP_SITES_GIVEN     */
   double threshold;       /* Gamma (gradient rule) or theta (band rule)                       */
   double sbar;            /* S-bar > 0 of Eq. (relation); varphi = phi / S-bar                */
-  int storage;            /* CGEVAP_F64, F32, F16DEV, BF16DEV, F32RC, F16RC or BF16RC        */
+  int storage;            /* CGEVAP_F64, F32, F16DEV, BF16DEV, F32RC, F16RC, BF16RC or F32X  */
 } cgevap_params;
 
 typedef struct cgevap_ledger {
@@ -324,7 +332,8 @@ CGEVAP_API int cgevap_adjoint_release(cgevap_sim* sim);
 /* ---- ensembles: many independent lattices in one persistent launch ---------------------------
  * An ensemble advances n independent members (D2Q9 and D3Q19 lattices of any sizes, each with its
  * own densities, relaxation times, surface tension, recoloring, site rule, threshold, S-bar,
- * flux and solids; FP32 or FP64 storage, mixed freely) by one cooperative persistent kernel
+ * flux and solids; FP32 or FP64 storage, mixed freely, or F32X throughout) by one cooperative
+ * persistent kernel
  * launch per call, captured
  * once in a CUDA graph and replayed.  Each member is a full cgevap_sim reachable with
  * cgevap_ensemble_member: set its flux, solids and initial state, read its macros, mask and
@@ -333,9 +342,10 @@ CGEVAP_API int cgevap_adjoint_release(cgevap_sim* sim);
 typedef struct cgevap_ens cgevap_ens;
 
 /* Create members[0..n-1] (each validated like cgevap_create; storage must be CGEVAP_F32 or
- * CGEVAP_F64, else UNSUPPORTED) and plan the work list with a default tiling.  An ensemble whose
- * members are all FP32 runs four CTAs per SM; one with FP64 members runs two (the FP64 step needs
- * more registers).  *out is NULL on failure. */
+ * CGEVAP_F64, mixed freely, or CGEVAP_F32X for every member; else UNSUPPORTED) and plan the work
+ * list with a default tiling.  An ensemble whose members are all FP32 (or all F32X) runs four
+ * CTAs per SM; one with FP64 members runs two (the FP64 step needs more registers).  *out is NULL
+ * on failure. */
 CGEVAP_API int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out);
 /* Free the ensemble and all its members.  NULL is accepted. */
 CGEVAP_API int cgevap_ensemble_destroy(cgevap_ens* ens);

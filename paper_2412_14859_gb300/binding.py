@@ -16,9 +16,9 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libcgevap.so")
 
-F64, F32, F16DEV, BF16DEV, F32RC, F16RC, BF16RC = 0, 1, 2, 3, 4, 5, 6
+F64, F32, F16DEV, BF16DEV, F32RC, F16RC, BF16RC, F32X = 0, 1, 2, 3, 4, 5, 6, 7
 STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV, "f32rc": F32RC,
-           "f16rc": F16RC, "bf16rc": BF16RC}
+           "f16rc": F16RC, "bf16rc": BF16RC, "f32x": F32X}
 DTYPE_F64, DTYPE_F32 = 0, 1
 SITES_GRADIENT, SITES_BAND, SITES_GIVEN = 0, 1, 2
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NAN", -6: "UNSUPPORTED", -7: "IO"}
@@ -379,7 +379,7 @@ def all_signatures():
 
 class Ensemble:
     """Independent lattices advanced together by one persistent launch; storage "f32" or "f64",
-    one for all members or a list with one per member."""
+    one for all members or a list with one per member, or "f32x" for all members."""
 
     def __init__(self, cases, storage="f32"):
         arr = (Params * len(cases))()

@@ -48,7 +48,7 @@ std::string validate(const cgevap_params* p) {
   if (p->site_rule != CGEVAP_SITES_GRADIENT && p->site_rule != CGEVAP_SITES_BAND &&
       p->site_rule != CGEVAP_SITES_GIVEN)
     return "unknown site rule";
-  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_BF16RC) return "unknown storage";
+  if (p->storage < CGEVAP_F64 || p->storage > CGEVAP_F32X) return "unknown storage";
   return "";
 }
 
@@ -108,6 +108,7 @@ int cgevap::internal_storage(int api_storage) {
     case CGEVAP_F32RC: return ST_RC;
     case CGEVAP_F16RC: return ST_H16RC;
     case CGEVAP_BF16RC: return ST_B16RC;
+    case CGEVAP_F32X: return ST_F32X;
     default: return -1;
   }
 }
@@ -122,8 +123,11 @@ AuxArgs cgevap::aux_of(const cgevap_sim* s) {
   a.ph = s->ph;
   mirror_floats(a.ph);
   a.q = s->p.q;
-  // the recolour-on-pull layouts hold an imported state as FP32 pairs until the next step
-  a.storage = is_recolour_on_pull(s->p.storage) && s->rc_pairs ? ST_F32 : internal_storage(s->p.storage);
+  // the recolour-on-pull layouts hold an imported state as FP32 pairs until the next step; the
+  // exact-mass FP32 pairs are FP32 pairs to every kernel but the step
+  a.storage = (is_recolour_on_pull(s->p.storage) && s->rc_pairs) || s->p.storage == CGEVAP_F32X
+                  ? ST_F32
+                  : internal_storage(s->p.storage);
   a.rho_r_in = s->p.rho_r_in;
   a.rho_b_in = s->p.rho_b_in;
   return a;
@@ -144,6 +148,7 @@ KernelRef kernel_for(int q, int storage, int variant, bool pairs_in = false) {
   switch (storage) {
     case CGEVAP_F64: return step_kernel_f64(q, variant);
     case CGEVAP_F32: return step_kernel_f32(q, variant);
+    case CGEVAP_F32X: return step_kernel_f32x(q, variant);
     case CGEVAP_F32RC: return step_kernel_rc(q, variant, pairs_in);
     case CGEVAP_F16RC:
     case CGEVAP_BF16RC: return step_kernel_rc16(q, internal_storage(storage), variant, pairs_in);
@@ -810,7 +815,8 @@ double cgevap_bytes_per_update(const cgevap_sim* s) {
   double pops;
   switch (s->p.storage) {
     case CGEVAP_F64: pops = 2.0 * 2 * Q * 8; break;
-    case CGEVAP_F32: pops = 2.0 * 2 * Q * 4; break;
+    case CGEVAP_F32:
+    case CGEVAP_F32X: pops = 2.0 * 2 * Q * 4; break;
     case CGEVAP_F32RC: pops = 2.0 * (Q * 4 + 16); break;
     case CGEVAP_F16RC:
     case CGEVAP_BF16RC: pops = 2.0 * (8 + 16 + 4 + (Q - 1) * 2); break;  // rest pair, record, Rf, deviations

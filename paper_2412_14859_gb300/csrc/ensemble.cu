@@ -6,8 +6,9 @@
 // the single-lattice step kernel splits it.  A D3Q19 item fills a 128-thread CTA (32 x 4 tile;
 // four CTAs per SM, as the fastest single-lattice step); D2Q9 items are narrower and run G at a
 // time in one CTA, one per group of 128/G threads (row tiles of 128/G cells), with their barrier
-// rounds padded to the longest chunk of the pack.  Members store FP32 or FP64 populations; a
-// pack holds items of one storage only, so every barrier round of a CTA runs the same code.
+// rounds padded to the longest chunk of the pack.  Members store FP32 or FP64 populations, or
+// all of them FP32 pairs with exact colour masses; a pack holds items of one storage only, so
+// every barrier round of a CTA runs the same code.
 // CTAs take items (or packs) from a counter, meet at a grid barrier after every step, and fold
 // the per-item ledger partials of each member in item order (deterministic).  Every wait is
 // bounded (4 s by default, settable from the host); a barrier that gives up sets the status
@@ -35,7 +36,7 @@ struct EnsMember {
   uint8_t* mask[2];
   DevLedger* ledger;
   int q;
-  int storage;          // ST_F32 or ST_F64
+  int storage;          // ST_F32 or ST_F64 (an all-F32X ensemble labels its members ST_F32)
   int item0, nitem;     // its items: [item0, item0 + nitem) of the concatenated list (0: paused)
 };
 
@@ -89,8 +90,15 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* status,
 constexpr int kEnsThreads = 128;  // threads per CTA
 constexpr int kEnsTy = 4;         // D3Q19 item tile: 32 x kEnsTy columns
 
-// Member storages a kernel instantiation handles: FP32 only, FP64 only, or both.
-enum { kEnsF32 = 0, kEnsF64 = 1, kEnsMixed = 2 };
+// Member storages a kernel instantiation handles: FP32 only, FP64 only, both, or FP32 pairs with
+// exact colour masses only.
+enum { kEnsF32 = 0, kEnsF64 = 1, kEnsMixed = 2, kEnsF32X = 3 };
+
+// The FP32 storage code of the ensemble's FP32 members under MODE.
+template <int MODE>
+constexpr int ens_s32() {
+  return MODE == kEnsF32X ? ST_F32X : ST_F32;
+}
 
 // Shared memory of one D2Q9 group / one D3Q19 item of storage S.
 template <int G, int S>
@@ -99,9 +107,10 @@ constexpr int ens_group_smem() {
 }
 
 template <int G, int MODE>
-__global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
+__global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 || MODE == kEnsF32X ? 4 : 2)
     cg_ensemble_kernel(const __grid_constant__ EnsArgs E) {
   constexpr int NT = kEnsThreads;
+  constexpr int S32 = ens_s32<MODE>();
   constexpr int GT = NT / G;  // threads per D2Q9 group
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double gsum_d[NT / 32];
@@ -137,8 +146,8 @@ __global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
         A.mask_out = M.mask[c ^ 1];
         const bool f64 = MODE == kEnsF64 || (MODE == kEnsMixed && M.storage == ST_F64);
         if (MODE != kEnsF64 && !f64)
-          step_tile<19, ST_F32, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
-        else if (MODE != kEnsF32)
+          step_tile<19, S32, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
+        else if (MODE == kEnsF64 || MODE == kEnsMixed)
           step_tile<19, ST_F64, 32, kEnsTy, 1>(A, it.y, it.z, smem, n, d);
         block_sum<NT>(n, d);
         if (tid == 0) {
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
         // the pack's storage: that of its first item, which is never a filler
         const bool f64 = MODE == kEnsF64 ||
                          (MODE == kEnsMixed && E.members[E.items[E.n3 + pack * G].x].storage == ST_F64);
-        unsigned char* gs = smem + grp * (f64 ? ens_group_smem<G, ST_F64>() : ens_group_smem<G, ST_F32>());
+        unsigned char* gs = smem + grp * (f64 ? ens_group_smem<G, ST_F64>() : ens_group_smem<G, S32>());
         if (it.x >= 0) {
           const EnsMember& M = E.members[it.x];
           StepArgs A = M.a;
@@ -163,8 +172,8 @@ __global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
           A.mask_in = M.mask[c];
           A.mask_out = M.mask[c ^ 1];
           if (MODE != kEnsF64 && !f64)
-            step_tile<9, ST_F32, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
-          else if (MODE != kEnsF32)
+            step_tile<9, S32, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
+          else if (MODE == kEnsF64 || MODE == kEnsMixed)
             step_tile<9, ST_F64, GT, 1, 1>(A, it.y, it.z, gs, n, d, gtid, iters);
         } else {
           for (int r = 0; r < 1 + iters; ++r) __syncthreads();  // same barrier rounds, no work
@@ -228,13 +237,14 @@ __global__ void __launch_bounds__(kEnsThreads, MODE == kEnsF32 ? 4 : 2)
 // Dynamic shared memory of the ensemble kernel for group count G and member storages MODE.
 template <int G, int MODE>
 static int ens_smem() {
-  constexpr int b32 = G * ens_group_smem<G, ST_F32>() > TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES
-                          ? G * ens_group_smem<G, ST_F32>()
-                          : TileSmem<19, ST_F32, 32, kEnsTy, 1>::BYTES;
+  constexpr int S32 = ens_s32<MODE>();
+  constexpr int b32 = G * ens_group_smem<G, S32>() > TileSmem<19, S32, 32, kEnsTy, 1>::BYTES
+                          ? G * ens_group_smem<G, S32>()
+                          : TileSmem<19, S32, 32, kEnsTy, 1>::BYTES;
   constexpr int b64 = G * ens_group_smem<G, ST_F64>() > TileSmem<19, ST_F64, 32, kEnsTy, 1>::BYTES
                           ? G * ens_group_smem<G, ST_F64>()
                           : TileSmem<19, ST_F64, 32, kEnsTy, 1>::BYTES;
-  return MODE == kEnsF32 ? b32 : (MODE == kEnsF64 ? b64 : (b32 > b64 ? b32 : b64));
+  return MODE == kEnsF32 || MODE == kEnsF32X ? b32 : (MODE == kEnsF64 ? b64 : (b32 > b64 ? b32 : b64));
 }
 
 template <int G, int MODE>
@@ -263,7 +273,7 @@ struct cgevap_ens {
   unsigned int* d_bar = nullptr;
   int* d_status = nullptr;
   size_t items_cap = 0;
-  int mode = kEnsF32;                  // member storages (kEnsF32 / kEnsF64 / kEnsMixed)
+  int mode = kEnsF32;                  // member storages (kEnsF32 / kEnsF64 / kEnsMixed / kEnsF32X)
   std::vector<int> active;             // 0: member paused (no items)
   unsigned long long barrier_ns = 4000000000ull;
   int skip_cta = -1, skip_step = -1;   // test hook of the grid barrier
@@ -303,6 +313,8 @@ const void* kernel_for_groups(int g, int mode) {
     case 4 * 4 + kEnsF64: return ens_fn<4, kEnsF64>();
     case 2 * 4 + kEnsMixed: return ens_fn<2, kEnsMixed>();
     case 4 * 4 + kEnsMixed: return ens_fn<4, kEnsMixed>();
+    case 2 * 4 + kEnsF32X: return ens_fn<2, kEnsF32X>();
+    case 4 * 4 + kEnsF32X: return ens_fn<4, kEnsF32X>();
     default: return nullptr;
   }
 }
@@ -314,6 +326,8 @@ int smem_for_groups(int g, int mode) {
     case 4 * 4 + kEnsF64: return ens_smem<4, kEnsF64>();
     case 2 * 4 + kEnsMixed: return ens_smem<2, kEnsMixed>();
     case 4 * 4 + kEnsMixed: return ens_smem<4, kEnsMixed>();
+    case 2 * 4 + kEnsF32X: return ens_smem<2, kEnsF32X>();
+    case 4 * 4 + kEnsF32X: return ens_smem<4, kEnsF32X>();
     default: return 0;
   }
 }
@@ -497,15 +511,20 @@ int cgevap_ensemble_create(const cgevap_params* members, int n, cgevap_ens** out
   if (!e) return CGEVAP_ERR_OOM;
   e->n = n;
   cudaGetDevice(&e->device);
-  int seen = 0;  // bit 0: an FP32 member, bit 1: an FP64 member
+  int seen = 0;  // bit 0: an FP32 member, bit 1: an FP64 member, bit 2: an F32X member
   for (int j = 0; j < n; ++j) {
-    if (members[j].storage != CGEVAP_F32 && members[j].storage != CGEVAP_F64) {
+    const int st = members[j].storage;
+    if (st != CGEVAP_F32 && st != CGEVAP_F64 && st != CGEVAP_F32X) {
       cgevap_ensemble_destroy(e);
       return CGEVAP_ERR_UNSUPPORTED;
     }
-    seen |= members[j].storage == CGEVAP_F64 ? 2 : 1;
+    seen |= st == CGEVAP_F64 ? 2 : (st == CGEVAP_F32X ? 4 : 1);
   }
-  e->mode = seen == 1 ? kEnsF32 : (seen == 2 ? kEnsF64 : kEnsMixed);
+  if ((seen & 4) && seen != 4) {  // F32X members only with one another
+    cgevap_ensemble_destroy(e);
+    return CGEVAP_ERR_UNSUPPORTED;
+  }
+  e->mode = seen == 4 ? kEnsF32X : (seen == 1 ? kEnsF32 : (seen == 2 ? kEnsF64 : kEnsMixed));
   e->active.assign(n, 1);
   for (int j = 0; j < n; ++j) {
     cgevap_sim* s = nullptr;

@@ -141,8 +141,14 @@ __host__ __device__ constexpr uint32_t dirs_where(int axis, int sign) {
 //   the moving populations will deliver, so the mass of each colour a cell stores is its exact
 //   post-exchange mass up to the rounding of the rest pair.  ST_H16RCI / ST_B16RCI: the same
 //   step reading FP32 pairs (an imported state).
+// ST_F32X: the FP32 pairs of ST_F32 with each colour's mass carried exactly through the step:
+//   the pulled pairs are summed per colour with Fast2Sum, the exchange's rounding is kept by
+//   TwoSum, and the rest pair is stored last as the exact post-exchange colour masses less the
+//   stored moving pairs, so the mass of each colour a cell passes on equals its exact mass up
+//   to one rounding of the rest pair (the FP32 arithmetic of the collision is otherwise that of
+//   ST_F32).
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_RC = 4, ST_RCI = 5, ST_H16RC = 6,
-       ST_B16RC = 7, ST_H16RCI = 8, ST_B16RCI = 9 };
+       ST_B16RC = 7, ST_H16RCI = 8, ST_B16RCI = 9, ST_F32X = 10 };
 
 // Traits of a storage code: dev = per-colour 16-bit deviations; rc = writes a recolour-on-pull
 // layout; rc16 = that layout is the 16-bit one; rc_in = reads a recolour-on-pull layout (the
@@ -224,6 +230,17 @@ struct Rc16Storage {
   static constexpr int bytes_per_pop = 2;
 };
 template <>
+struct Storage<ST_F32X> : Storage<ST_F32> {};
+// Storages whose FP32 pairs carry each colour's mass exactly (ST_F32X).
+template <int S>
+struct ExactPairs {
+  static constexpr bool value = false;
+};
+template <>
+struct ExactPairs<ST_F32X> {
+  static constexpr bool value = true;
+};
+template <>
 struct Storage<ST_H16RC> : Rc16Storage<Half16, false> {};
 template <>
 struct Storage<ST_B16RC> : Rc16Storage<BHalf16, false> {};
@@ -291,6 +308,7 @@ __host__ inline size_t state_bytes(int storage, int q, long long nstore) {
   switch (storage) {
     case ST_F64: return (size_t)q * nstore * sizeof(double2);
     case ST_F32:
+    case ST_F32X:
     case ST_RC:  // room for the FP32 pairs of an imported state
     case ST_RCI: return (size_t)q * nstore * sizeof(float2);
     case ST_H16RC:

@@ -32,6 +32,7 @@ struct KernelRef {
 };
 KernelRef step_kernel_f64(int q, int variant);
 KernelRef step_kernel_f32(int q, int variant);
+KernelRef step_kernel_f32x(int q, int variant);  // FP32 pairs, exact colour masses (step_f32.cu)
 KernelRef step_kernel_dev(int q, int storage, int variant);
 // Recolour-on-pull layout (step_rc.cu); pairs_in: the input state holds FP32 pairs (import).
 KernelRef step_kernel_rc(int q, int variant, bool pairs_in);

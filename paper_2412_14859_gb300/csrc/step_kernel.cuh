@@ -617,7 +617,7 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
         rc_pop[si + dimg[j]] = fi0;
         rc_rec[si + dimg[j]] = rec;
       }
-  } else if constexpr (!Storage<S>::dev) {
+  } else if constexpr (!Storage<S>::dev && !ExactPairs<S>::value) {
     IO::store(A.pout, A.g.nstore, 0, si, f0.r, f0.b, f0, ph);
     if (GHOSTS && nimg)
       for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], f0.r, f0.b, f0, ph);
@@ -716,6 +716,10 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     } else {
       IO::store(A.pout, A.g.nstore, i, si, fri, fi - fri, f0, ph);
       IO::store(A.pout, A.g.nstore, j, si, frj, fj - frj, f0, ph);
+      if constexpr (ExactPairs<S>::value) {  // what the stored moving pairs carry, exactly
+        fast_two_sum_acc(rc_out_hi, rc_out_lo, make_float2(fri, fi - fri));
+        fast_two_sum_acc(rc_out_hi, rc_out_lo, make_float2(frj, fj - frj));
+      }
       if (GHOSTS && nimg) {  // periodic ghost images: cells within two of a periodic x or y edge
         for (int k = 0; k < nimg; ++k) {
           IO::store(A.pout, A.g.nstore, i, si + dimg[k], fri, fi - fri, f0, ph);
@@ -723,6 +727,19 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
         }
       }
     }
+  }
+  if constexpr (ExactPairs<S>::value) {
+    // the rest pair: the exact colour masses (rr + lr, rb + lb) less the stored moving pairs
+    // (rc_out_hi + rc_out_lo), as for the 16-bit recolour-on-pull layout
+    const float2 t = make_float2(float(rr), float(rb));
+    const float2 s2 = sub2(t, rc_out_hi);
+    const float2 e2 = make_float2(two_sum_err(t.x, -rc_out_hi.x, s2.x),
+                                  two_sum_err(t.y, -rc_out_hi.y, s2.y));
+    const float2 small = __fadd2_rn(e2, sub2(make_float2(float(lr), float(lb)), rc_out_lo));
+    const float2 r0 = __fadd2_rn(s2, small);
+    IO::store(A.pout, A.g.nstore, 0, si, r0.x, r0.y, f0, ph);
+    if (GHOSTS && nimg)
+      for (int j = 0; j < nimg; ++j) IO::store(A.pout, A.g.nstore, 0, si + dimg[j], r0.x, r0.y, f0, ph);
   }
   if constexpr (Storage<S>::rc16) {
     // the rest pair carries the exact colour masses (rr + lr, rb + lb) less what the moving
@@ -879,6 +896,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
   R(*ring)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ring_mem);
   // deviation storage: rest pairs of the tile plus a two-cell ring, planes m .. m+2
   constexpr bool DEV = Storage<S>::dev;
+  constexpr bool EXACTP = ExactPairs<S>::value;      // FP32 pairs with exact colour masses
   constexpr bool RCIN = Storage<S>::rc_in;          // reads a recolour-on-pull layout
   constexpr bool RC16IN = RCIN && Storage<S>::rc16;  // ... the 16-bit one
   constexpr bool STAGE = DEV || RCIN;    // pulls read per-source data staged in shared memory
@@ -1159,6 +1177,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
             out[c].lr = __fadd_rn(out[c].lr, two_sum_err(sr, -out[c].e, out[c].rr));
             out[c].lb = __fadd_rn(out[c].lb, two_sum_err(sb, out[c].e, out[c].rb));
           }
+        } else if constexpr (EXACTP) {
+          // colour totals without rounding error, rest pair first (its hi parts are the plain
+          // sums, so rho^N is that of the other storages' exchange), then the exchange (TwoSum)
+          float2 acc = make_float2(g[c][0].r, g[c][0].b), lo = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int i = 1; i < Q; ++i) fast_two_sum_acc(acc, lo, make_float2(g[c][i].r, g[c][i].b));
+          rn = exchange_from_sums<S>(A, cells[c], acc.x, acc.y, out[c].rr, out[c].rb, out[c].e,
+                                     out[c].flags, out[c].irho);
+          out[c].lr = __fadd_rn(lo.x, two_sum_err(acc.x, -out[c].e, out[c].rr));
+          out[c].lb = __fadd_rn(lo.y, two_sum_err(acc.y, out[c].e, out[c].rb));
+          g[c][0].r -= out[c].e;
+          g[c][0].b += out[c].e;
         } else
           rn = site_exchange<Q, S>(A, cells[c], g[c], out[c].rr, out[c].rb, out[c].e,
                                    out[c].flags, out[c].irho);
@@ -1235,7 +1265,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
         }
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
-      if constexpr (DEV || RC16IN)
+      if constexpr (DEV || RC16IN || EXACTP)
         epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
                                 cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
                                 nloc, rem, cur[c].lr, cur[c].lb);

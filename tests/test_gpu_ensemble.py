@@ -225,3 +225,44 @@ def test_benchmark_mix_members_equal_standalone_and_oracle():
         assert rel_linf(g["rho_r"].cpu().numpy(), run.macros()["rho_r"]) <= 1e-5, cases[j].name
         assert rel_linf(g["rho_b"].cpu().numpy(), run.macros()["rho_b"]) <= 1e-5, cases[j].name
     ens.close()
+
+
+def test_exact_mass_members():
+    """An ensemble whose members all store FP32 pairs with exact colour masses (f32x): each
+    member equals its standalone f32x run within the FP32 parity tolerance and carries the same
+    red mass to 1e-7; f32x cannot be mixed with other storages in one launch; at phi = 1e-6 the
+    sweep's drop removes the red mass its FP64 ledger records (to 1e-3 after 2e5 steps, where
+    FP32 pairs remove about a fifth less)."""
+    from dataclasses import replace
+
+    from paper_2412_14859_gb300.binding import CgevapError, Ensemble
+    cases = _three()
+    ens = Ensemble(cases, "f32x")
+    for sim, case in zip(ens.members, cases):
+        init_member(sim, case)
+    ens.step(6).step(7)
+    ens.status()
+    for sim, case in zip(ens.members, cases):
+        ref = gpu_sim(case, "f32x")
+        ref.step(13)
+        a, b = sim.populations(torch.float64), ref.populations(torch.float64)
+        assert (a - b).abs().max().item() <= 1e-5 * b.abs().max().item(), case.name
+        ma, mb = float(sim.macros()["rho_r"].sum()), float(ref.macros()["rho_r"].sum())
+        assert abs(ma - mb) <= 1e-7 * mb, case.name
+        assert sim.ledger()["steps"] == 13
+        ref.close()
+    ens.close()
+    with pytest.raises(CgevapError, match="UNSUPPORTED"):
+        Ensemble(cases, ["f32x", "f32", "f32x"])
+    drop = replace(inputs.drop_2d(1e-6, 0.3), sbar=1.0285)
+    ens = Ensemble([drop, drop], ["f32x", "f32x"])
+    m0 = []
+    for sim in ens.members:
+        init_member(sim, drop)
+        m0.append(float(sim.macros()["rho_r"].sum()))
+    ens.step(100000).step(100000)
+    ens.status()
+    for sim, m in zip(ens.members, m0):
+        lost = m - float(sim.macros()["rho_r"].sum())
+        assert abs(lost / sim.ledger()["evaporated"] - 1.0) <= 1e-3
+    ens.close()

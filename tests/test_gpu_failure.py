@@ -20,7 +20,7 @@ from paper_2412_14859_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-STORAGES = ["f64", "f32", "f16dev", "bf16dev", "f32rc", "f16rc", "bf16rc"]
+STORAGES = ["f64", "f32", "f16dev", "bf16dev", "f32rc", "f16rc", "bf16rc", "f32x"]
 
 
 def small_drop(q):
