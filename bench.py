@@ -548,7 +548,8 @@ def run_sweep_2d(args):
     """The D2Q9 drop sweep to R0/2: every (phi, theta) case with its band-rule S-bar, equilibrated
     3000 steps with the flux off, then evaporated; R = sqrt(V / pi) of the liquid area against
     R0 - phi t / rho_l at R/R0 = 3/4 and 1/2; each member is paused once it reaches its second
-    mark, and the launches are cut into calls of at most 1e5 steps."""
+    mark (the tiling tuned again for the members left), and the launches are cut into calls of
+    at most 1e5 steps."""
     import numpy as np
     import torch
     from dataclasses import replace
@@ -565,6 +566,7 @@ def run_sweep_2d(args):
     for sim, c in zip(ens.members, cases):
         sim.set_flux(0.0)
         sim.init_equilibrium(torch.from_numpy(c.phase()).cuda(), torch.from_numpy(c.noise_array()).cuda())
+    ens.autotune(probe_steps=20)
     ens.step(3000)
     R0, rho, m0 = [], [], []
     for sim, c in zip(ens.members, cases):
@@ -576,7 +578,7 @@ def run_sweep_2d(args):
         sim.reset_ledger()
     marks = [[(1.0 - f) * R0[j] * rho[j] / c.phi for f in (0.75, 0.5)] for j, c in enumerate(cases)]
     err = [[None, None] for _ in cases]
-    active, t = set(range(len(cases))), 0
+    active, t, retune = set(range(len(cases))), 0, False
     while active:
         nxt = min(int(round(marks[j][k])) for j in active for k in (0, 1) if err[j][k] is None)
         ens.step(min(nxt - t, 100000))
@@ -591,6 +593,10 @@ def run_sweep_2d(args):
                 active.discard(j)
                 if active:
                     ens.set_active(j, False)
+                    retune = True
+        if retune:  # fewer members: shorter chunks spread the rest over more CTAs
+            ens.autotune(probe_steps=20)
+            retune = False
     ens.status()
     rows = []
     for j, c in enumerate(cases):

@@ -391,9 +391,11 @@ CGEVAP_API int cgevap_ensemble_grid(const cgevap_ens* ens);
 CGEVAP_API int cgevap_ensemble_set_tuning(cgevap_ens* ens, int groups, int planes_3d, int planes_2d);
 CGEVAP_API int cgevap_ensemble_get_tuning(const cgevap_ens* ens, int* groups, int* planes_3d,
                                           int* planes_2d);
-/* Autotuner: times probe_steps steps of every candidate tiling on the ensemble as it is (its
- * states, site bytes and ledgers are backed up first and restored after), keeps the fastest and
- * writes its time per step to *best_ms (may be NULL).  Needs room for one copy of the states. */
+/* Autotuner: times probe_steps steps of every candidate tiling (groups 4 / 2, D3Q19 chunks of
+ * 16-128 planes, D2Q9 chunks of 4-64 rows; only the values that matter for the active members)
+ * on the ensemble as it is (its states, site bytes and ledgers are backed up first and restored
+ * after), keeps the fastest and writes its time per step to *best_ms (may be NULL).  Needs room
+ * for one copy of the states.  Pausing members changes the work: tune again after it. */
 CGEVAP_API int cgevap_ensemble_autotune(cgevap_ens* ens, int probe_steps, double* best_ms);
 
 /* ---- one timestep without any allocation -------------------------------------------------

@@ -724,7 +724,13 @@ int cgevap_ensemble_autotune(cgevap_ens* e, int probe_steps, double* best_ms) {
   }
   const int cand_g[] = {4, 2};
   const int cand_p3[] = {16, 32, 64, 128};
-  const int cand_p2[] = {16, 32, 64};
+  // short D2Q9 chunks for few small members (more items to spread over the resident CTAs)
+  const int cand_p2[] = {4, 8, 16, 32, 64};
+  // a lattice kind with no active member leaves its chunk length (and, for D2Q9, the group
+  // count) without effect: probe one value of it
+  bool has3 = false, has2 = false;
+  for (int j = 0; j < e->n; ++j)
+    if (e->active[j]) (e->params[j].q == 19 ? has3 : has2) = true;
   double best = 1e300;
   int bg = e->groups, b3 = e->pc3, b2 = e->pc2;
   cudaEvent_t t0, t1;
@@ -734,6 +740,7 @@ int cgevap_ensemble_autotune(cgevap_ens* e, int probe_steps, double* best_ms) {
   for (int g : cand_g)
     for (int p3 : cand_p3)
       for (int p2 : cand_p2) {
+        if ((!has2 && (g != cand_g[0] || p2 != 16)) || (!has3 && p3 != cand_p3[0])) continue;
         e->groups = g;
         e->pc3 = p3;
         e->pc2 = p2;
