@@ -95,6 +95,7 @@ void setup_physics(cgevap_sim* s) {
     ph.scale = 1.0f;
   }
   ph.inv_scale = 1.0f / ph.scale;
+  ph.sum_base = sum_base_for(p.rho_r_in, p.rho_b_in);
 }
 
 }  // namespace

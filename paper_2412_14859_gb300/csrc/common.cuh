@@ -73,11 +73,22 @@ struct Physics {
   const void* phi_field;         // per-cell phi (double for ST_F64, float otherwise) or nullptr
   float kap_r[19], kap_b[19];    // deviation storage: phi_i(alpha_k) / phi_0(alpha_k)
   float scale, inv_scale;        // deviation storage: power-of-two scale of the deviations
+  float sum_base;                // error-free colour sums start here: a power of two at least
+                                 // any single population (0: from the first term)
   // FP32 copies of the constants above (rounded to nearest, as a device-side conversion would
   // round them), so FP32 kernels execute no FP64 instruction; filled by mirror_floats().
   float f_inv_tau_r, f_inv_tau_b, f_alpha_r, f_alpha_b, f_amp, f_beta, f_threshold, f_varphi,
       f_inv_sbar;
 };
+
+// Start of the error-free colour sums: a power of two at least four times the larger initial
+// density (a single population is below the density of its cell).
+__host__ inline float sum_base_for(double rho_r_in, double rho_b_in) {
+  const double r = 4.0 * (rho_r_in > rho_b_in ? rho_r_in : rho_b_in);
+  float b = 1.0f;
+  while (b < r && b < 1e30f) b *= 2.0f;
+  return b;
+}
 
 // Refresh the FP32 copies; every launch that passes a Physics to a kernel calls this first.
 __host__ __device__ inline void mirror_floats(Physics& ph) {

@@ -197,6 +197,7 @@ extern "C" CGEVAP_API int cgevap_step_static_scratch(
     ph.scale = 1.0f;
   }
   ph.inv_scale = 1.0f / ph.scale;
+  ph.sum_base = sum_base_for(p->rho_r_in, p->rho_b_in);
 
   KernelRef k = p->storage == CGEVAP_F64   ? step_kernel_f64(p->q, 0)
                 : p->storage == CGEVAP_F32 ? step_kernel_f32(p->q, 0)

@@ -220,11 +220,12 @@ __global__ void __launch_bounds__(TX* TY, MINB) cg_step_dev_kernel(const __grid_
         V2<R> g[Q];
         dev_decode<Q, S, RY, RX>(A.ph, raw[c], out[c].bits, lx + 2, L::D3 ? ly0 + c * TY + 2 : 0,
                                  ps, rest_ring, g);
-        // colour totals without rounding error (the rest pair first: the largest term), then
-        // Eq. (exchange) with its own rounding error (the collision re-decodes g)
-        float2 hi = make_float2(g[0].r, g[0].b), lo = make_float2(0.0f, 0.0f);
+        // colour totals without rounding error (from the base B, rest pair first), rounded
+        // to nearest, then Eq. (exchange) with its own rounding error (the collision re-decodes g)
+        float2 hi = sum_start(A.ph), lo = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) fast_two_sum_acc(hi, lo, make_float2(g[i].r, g[i].b));
+        for (int i = 0; i < Q; ++i) fast_two_sum_acc(hi, lo, make_float2(g[i].r, g[i].b));
+        sum_finish(A.ph, hi, lo);
         rn = exchange_from_sums<S>(A, cells[c], hi.x, hi.y, out[c].rr, out[c].rb, out[c].e,
                                    out[c].flags, out[c].irho);
         out[c].lr = __fadd_rn(lo.x, two_sum_err(hi.x, -out[c].e, out[c].rr));

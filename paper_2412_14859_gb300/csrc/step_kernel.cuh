@@ -215,6 +215,26 @@ __device__ __forceinline__ void fast_two_sum_acc(float2& hi, float2& lo, float2 
   lo = __fadd2_rn(lo, sub2(v, sub2(s, hi)));
   hi = s;
 }
+// TwoSum error of s = fl(a + b) per component (no ordering needed)
+__device__ __forceinline__ float2 two_sum_err2(float2 a, float2 b, float2 s) {
+  const float2 bb = sub2(s, a);
+  return __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// A running error-free sum per colour starts at the power of two B = Physics::sum_base, which is
+// at least any single population, so Fast2Sum's condition |hi| >= |v| holds for every term.
+// Started from the first term instead, a larger later term (a red population arriving at a
+// gas-side interface cell, whose own red is small) leaves that term's error inexact.  hi - B is
+// exact (Sterbenz: B/2 <= hi <= 2B, or hi and B both multiples of ulp(B)).
+__device__ __forceinline__ float2 sum_start(const Physics& ph) {
+  return make_float2(ph.sum_base, ph.sum_base);
+}
+// (hi, lo) started at B -> hi = fl(total), lo = total - hi (up to lo's own roundings)
+__device__ __forceinline__ void sum_finish(const Physics& ph, float2& hi, float2& lo) {
+  const float2 h = sub2(hi, sum_start(ph));
+  const float2 t = __fadd2_rn(h, lo);
+  lo = two_sum_err2(h, lo, t);
+  hi = t;
+}
 
 // Pull one cell (Eq. Stream, pull form).  Sources are the slot's wrap-aware in-plane offsets plus
 // the plane offsets; where the source is solid or beyond a wall the population leaving the cell
@@ -271,7 +291,8 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
   uint32_t raw[Q];
   const float2 r0 = restbox(ps[1], ey, ex);
   g[0] = {r0.x + r0.y, 0.0f};
-  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
+  float2 acc = sum_start(ph), lo = make_float2(0.0f, 0.0f);
+  fast_two_sum_acc(acc, lo, r0);
   if (sbits == 0) {  // no link bounces back: every address is a fixed offset
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -318,6 +339,7 @@ __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl,
       g[i] = {v.x + v.y, 0.0f};
     }
   }
+  sum_finish(ph, acc, lo);
   sr = acc.x;
   sb = acc.y;
   lr = lo.x;
@@ -442,7 +464,8 @@ __device__ __forceinline__ void rc16_decode(const StepArgs& A, uint32_t sbits,
   using L = Lattice<Q>;
   using H = typename Storage<S>::half_t;
   const float inv_scale = A.ph.inv_scale;
-  float2 acc = r0, lo = make_float2(0.0f, 0.0f);
+  float2 acc = sum_start(A.ph), lo = make_float2(0.0f, 0.0f);
+  fast_two_sum_acc(acc, lo, r0);
   g[0] = {r0.x + r0.y, 0.0f};
   if (sbits == 0) {
 #pragma unroll
@@ -471,6 +494,7 @@ __device__ __forceinline__ void rc16_decode(const StepArgs& A, uint32_t sbits,
       g[i] = {f, 0.0f};
     }
   }
+  sum_finish(A.ph, acc, lo);
   sr = acc.x;
   sb = acc.y;
   lr = lo.x;
@@ -594,7 +618,7 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   // moving populations will deliver per colour, summed without rounding error (rc_out_hi + lo)
   float4 rc16_rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float rc16_rf = 0.0f;
-  float2 rc_out_hi = make_float2(0.0f, 0.0f), rc_out_lo = make_float2(0.0f, 0.0f);
+  float2 rc_out_hi = sum_start(ph), rc_out_lo = make_float2(0.0f, 0.0f);
   (void)rc16_rec;
   (void)rc16_rf;
   (void)rc_out_hi;
@@ -626,8 +650,9 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   // 1 / scale); the rest pair, stored last, takes it back so the cell's stored mass is its mass
   float2 dev_loss = make_float2(0.0f, 0.0f);
   (void)dev_loss;
-  // EXACT: the FP32 outputs summed per colour without rounding error, rest pair first
-  float2 out_hi = make_float2(float(f0.r), float(f0.b)), out_lo = make_float2(0.0f, 0.0f);
+  // EXACT: the FP32 outputs summed per colour without rounding error (from B), rest pair first
+  float2 out_hi = sum_start(ph), out_lo = make_float2(0.0f, 0.0f);
+  if constexpr (Storage<S>::dev && EXACT) fast_two_sum_acc(out_hi, out_lo, make_float2(float(f0.r), float(f0.b)));
   (void)out_hi;
   (void)out_lo;
   static_assert(opposites_adjacent<L>(), "directions (i, i+1), i odd, must be opposite");
@@ -730,7 +755,8 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   }
   if constexpr (ExactPairs<S>::value) {
     // the rest pair: the exact colour masses (rr + lr, rb + lb) less the stored moving pairs
-    // (rc_out_hi + rc_out_lo), as for the 16-bit recolour-on-pull layout
+    // (rc_out_hi - B + rc_out_lo), as for the 16-bit recolour-on-pull layout
+    rc_out_hi = sub2(rc_out_hi, sum_start(ph));  // exact
     const float2 t = make_float2(float(rr), float(rb));
     const float2 s2 = sub2(t, rc_out_hi);
     const float2 e2 = make_float2(two_sum_err(t.x, -rc_out_hi.x, s2.x),
@@ -744,7 +770,8 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
   if constexpr (Storage<S>::rc16) {
     // the rest pair carries the exact colour masses (rr + lr, rb + lb) less what the moving
     // populations deliver (rc_out_hi + rc_out_lo): TwoSum of the large terms, then the small ones
-    // (the periodic images of the TMA family are not kept for this layout)
+    // (the periodic images of the TMA family are not kept for this layout); rc_out_hi - B exact
+    rc_out_hi = sub2(rc_out_hi, sum_start(ph));
     const float2 t = make_float2(float(rr), float(rb));
     const float2 s2 = sub2(t, rc_out_hi);
     const float2 e2 = make_float2(two_sum_err(t.x, -rc_out_hi.x, s2.x),
@@ -763,7 +790,9 @@ __device__ __forceinline__ void collide_store(const StepArgs& A, int si, int nim
     V2<R> f0c;
     if constexpr (EXACT) {
       // EXACT: delta = alpha_k times what the stored mass misses of the exact mass, (rr + lr)
-      // - (out_hi + out_lo); the high parts agree to a few ulps, so their difference is exact
+      // - (out_hi - B + out_lo); out_hi - B is exact and the high parts agree to a few ulps of
+      // B, so their difference is exact too
+      out_hi = sub2(out_hi, sum_start(ph));
       const float2 miss = __fadd2_rn(sub2(make_float2(rr, rb), out_hi),
                                      sub2(make_float2(lr, lb), out_lo));
       const float2 c = __ffma2_rn(make_float2(PHYS(R, ph, alpha_r), PHYS(R, ph, alpha_b)), miss,
@@ -1178,15 +1207,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
             out[c].lb = __fadd_rn(out[c].lb, two_sum_err(sb, out[c].e, out[c].rb));
           }
         } else if constexpr (EXACTP) {
-          // colour totals without rounding error, rest pair first (its hi parts are the plain
-          // sums, so rho^N is that of the other storages' exchange), then the exchange (TwoSum)
-          float2 acc = make_float2(g[c][0].r, g[c][0].b), lo = make_float2(0.0f, 0.0f);
+          // the plain sums of the FP32 pairs (those the ring cells form, so rho^N of a cell is
+          // the same in every tile that holds it) and the colour totals without rounding error
+          // (from B); what the exact totals exceed the plain ones by, and the exchange's own
+          // rounding (TwoSum), go to (lr, lb)
+          float2 plain = make_float2(0.0f, 0.0f);
+          float2 acc = sum_start(A.ph), lo = make_float2(0.0f, 0.0f);
 #pragma unroll
-          for (int i = 1; i < Q; ++i) fast_two_sum_acc(acc, lo, make_float2(g[c][i].r, g[c][i].b));
-          rn = exchange_from_sums<S>(A, cells[c], acc.x, acc.y, out[c].rr, out[c].rb, out[c].e,
-                                     out[c].flags, out[c].irho);
-          out[c].lr = __fadd_rn(lo.x, two_sum_err(acc.x, -out[c].e, out[c].rr));
-          out[c].lb = __fadd_rn(lo.y, two_sum_err(acc.y, out[c].e, out[c].rb));
+          for (int i = 0; i < Q; ++i) {
+            const float2 v = make_float2(g[c][i].r, g[c][i].b);
+            plain = __fadd2_rn(plain, v);
+            fast_two_sum_acc(acc, lo, v);
+          }
+          // (acc - B) and plain are both within a few ulps of B of the total: exact difference
+          lo = __fadd2_rn(sub2(sub2(acc, sum_start(A.ph)), plain), lo);
+          rn = exchange_from_sums<S>(A, cells[c], plain.x, plain.y, out[c].rr, out[c].rb,
+                                     out[c].e, out[c].flags, out[c].irho);
+          out[c].lr = __fadd_rn(lo.x, two_sum_err(plain.x, -out[c].e, out[c].rr));
+          out[c].lb = __fadd_rn(lo.y, two_sum_err(plain.y, out[c].e, out[c].rb));
           g[c][0].r -= out[c].e;
           g[c][0].b += out[c].e;
         } else

@@ -138,7 +138,7 @@ def test_small_flux_removes_the_ledgers_mass():
     after 2e5 steps; the D2Q9 sweep: 12.7 % less over 2e7).  The 16-bit recolour-on-pull layouts
     carry each colour's mass exactly up to one rounding of the rest pair per cell and step: over
     2e5 steps of the sweep's phi = 1e-6, theta = 0.3 drop they remove the ledger's red mass to
-    3.4e-4 of it (3e-6 of the drop's red mass), FP64 to 2.6e-10."""
+    2.0e-4 (FP16) and 3.0e-4 (BF16) of it (3e-6 of the drop's red mass), FP64 to 2.6e-10."""
     case = replace(inputs.drop_2d(1e-6, 0.3), sbar=1.0285)
     steps = 200000
     out = {}
