@@ -274,8 +274,8 @@ __device__ __forceinline__ void pull_cell(const StepArgs& A, const Slot& sl, int
 // colour-blind values and the two colour totals (Eq. exchange changes the totals, not the
 // colour-blind rest population), so that is what comes out: g_i = (f_i^r + f_i^b, 0) and
 // (sr, sb) = the sums of each colour over i; Q + 2 live values instead of 2Q.  (lr, lb) are the
-// rounding errors of those sums: sr + lr is the exact sum of the decoded values (the rest
-// population, summed first, is the largest term).
+// rounding errors of those sums: sr + lr is the exact sum of the decoded values (Fast2Sum from
+// the base B, see sum_start).
 template <int Q, int S, class RestBox>
 __device__ __forceinline__ void pull_cell_dev(const StepArgs& A, const Slot& sl, int si,
                                               PlaneOffsets po, uint32_t sbits, int ex, int ey,
@@ -418,8 +418,8 @@ __device__ __forceinline__ void pull_cell_rc(const StepArgs& A, const Slot& sl, 
 // (k = 1: this plane), so the source of direction i sits at the compile-time offset
 // -(c_i,b RX + c_i,a) from bx[1 + c_i,m].  The rest pair (f_0^r, f_0^b) is the cell's own, read
 // from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb) summed
-// rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact sum of
-// the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
+// with Fast2Sum from the base B, rest pair first, and their rounding errors (lr, lb): sr + lr is
+// the exact sum of the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
 // takes a path whose addresses are all fixed offsets; the others take the general one.
 // The global loads of pull_cell_rc16: the 16-bit values of the cell's pulled moving populations
 // (raw[i], i >= 1) and its own rest pair r0 (they need nothing staged).
@@ -509,8 +509,8 @@ __device__ __forceinline__ void rc16_decode(const StepArgs& A, uint32_t sbits,
 // (k = 1: this plane), so the source of direction i sits at the compile-time offset
 // -(c_i,b RX + c_i,a) from bx[1 + c_i,m].  The rest pair (f_0^r, f_0^b) is the cell's own, read
 // from global memory.  Output as pull_cell_dev: g_i = (f_i, 0), the colour totals (sr, sb) summed
-// rest pair first with Fast2Sum, and their rounding errors (lr, lb): sr + lr is the exact sum of
-// the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
+// with Fast2Sum from the base B, rest pair first, and their rounding errors (lr, lb): sr + lr is
+// the exact sum of the split values.  A cell none of whose links bounces back (sbits == 0, nearly every cell)
 // takes a path whose addresses are all fixed offsets; the others take the general one.
 template <int Q, int S, int RX>
 __device__ __forceinline__ void pull_cell_rc16(const StepArgs& A, const Slot& sl, int si,
