@@ -199,15 +199,16 @@ def measured_peaks():
 
 
 def kernel_hash() -> str:
-    """sha256 prefix of the step kernel's sources with their comments removed (a comment edit
-    leaves the kernel, and the traffic measured on it, as they were)."""
+    """sha256 prefix of the step kernel's sources with their comments removed and whitespace
+    runs collapsed (a comment edit leaves the kernel, and the traffic measured on it, as they
+    were)."""
     import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         src = open(os.path.join(ROOT, "paper_2412_14859_gb300", "csrc", f), encoding="utf-8").read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        h.update(src.encode())
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -203,3 +203,26 @@ def test_clock_samples_are_summarised(tmp_path):
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert not path.exists()  # the sample file is removed
     assert b.Clocks(0, enabled=False).stop() is None
+
+
+def test_traffic_follows_the_kernel_code_not_its_comments(tmp_path, monkeypatch):
+    """The committed DRAM-traffic figures stay attached to the step kernel while only comments
+    change, and are dropped once its code changes."""
+    import shutil
+    b = load_bench()
+    src = os.path.join(ROOT, "paper_2412_14859_gb300", "csrc")
+    fake = tmp_path / "paper_2412_14859_gb300" / "csrc"
+    fake.mkdir(parents=True)
+    for f in b.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), fake / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    h = b.kernel_hash()
+    (tmp_path / "profiles" / "step_traffic.txt").write_text(
+        f"# header\nstorage=f32 hash={h} cells=8 dram_read=1 dram_write=1 dram_bytes_per_cell=301.5\n")
+    assert b.ncu_traffic("f32", 192) == 301.5
+    k = fake / b.KERNEL_SOURCES[-1]
+    k.write_text(k.read_text() + "\n// a comment\n/* another\n one */\n")
+    assert b.kernel_hash() == h and b.ncu_traffic("f32", 192) == 301.5
+    k.write_text(k.read_text() + "\nstatic int changed_code = 1;\n")
+    assert b.kernel_hash() != h and b.ncu_traffic("f32", 192) is None
