@@ -234,6 +234,13 @@ CGEVAP_API int cgevap_volume(cgevap_sim* sim, double* dev_out);
  * clears the flag) if a bounded device-side wait of a step since the last call gave up. */
 CGEVAP_API int cgevap_get_ledger(cgevap_sim* sim, cgevap_ledger* host_out);
 
+/* The same record, copied asynchronously on the simulation's stream into host_out, which the
+ * caller owns: page-locked host memory (else the copy may run synchronously), valid and
+ * unread until the stream has passed this point.  A loop of steps can thus read the ledger after
+ * every step without waiting for the GPU.  The timeout flag of a device-side wait is neither
+ * read nor cleared: cgevap_get_ledger reports it.  Errors: ARG (NULL), CUDA. */
+CGEVAP_API int cgevap_get_ledger_async(cgevap_sim* sim, cgevap_ledger* host_out);
+
 /* Zero the ledger (asynchronous). */
 CGEVAP_API int cgevap_reset_ledger(cgevap_sim* sim);
 

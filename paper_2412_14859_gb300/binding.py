@@ -81,6 +81,7 @@ _SIGS = {
     "cgevap_adjoint_run": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "cgevap_adjoint_release": (ctypes.c_int, [_vp]),
     "cgevap_get_ledger": (ctypes.c_int, [_vp, ctypes.POINTER(Ledger)]),
+    "cgevap_get_ledger_async": (ctypes.c_int, [_vp, _vp]),
     "cgevap_reset_ledger": (ctypes.c_int, [_vp]),
     "cgevap_check_health": (ctypes.c_int, [_vp]),
     "cgevap_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
@@ -318,6 +319,22 @@ class Sim:
         L = Ledger()
         self._sync_stream()
         self._check(lib().cgevap_get_ledger(self._h, ctypes.byref(L)))
+        return {k: getattr(L, k) for k, _ in Ledger._fields_}
+
+    def ledger_async(self, out: torch.Tensor):
+        """Enqueue a copy of the ledger into `out`, a page-locked CPU uint8 tensor of at least 40
+        bytes (see ledger_from); it holds the record once the current stream has passed here."""
+        if out.device.type != "cpu" or out.dtype != torch.uint8 or out.numel() < ctypes.sizeof(Ledger):
+            raise ValueError("ledger_async needs a CPU uint8 tensor of at least 40 bytes")
+        if not out.is_pinned():
+            raise ValueError("ledger_async needs page-locked memory (pin_memory=True)")
+        self._sync_stream()
+        self._check(lib().cgevap_get_ledger_async(self._h, ctypes.c_void_p(out.data_ptr())))
+
+    @staticmethod
+    def ledger_from(buf: torch.Tensor) -> dict:
+        """The ledger record held in the first 40 bytes of a CPU uint8 tensor."""
+        L = Ledger.from_buffer_copy(bytes(buf[:ctypes.sizeof(Ledger)].numpy()))
         return {k: getattr(L, k) for k, _ in Ledger._fields_}
 
     def reset_ledger(self):

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/cgevap.h: handle lifetime, validation, launch planning and the
 // host side of every entry point.  No C++ exception or abort crosses the boundary.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -655,6 +656,22 @@ int cgevap_get_ledger(cgevap_sim* s, cgevap_ledger* out) {
   out->site_steps = d.site_steps;
   out->last_sites = d.last_sites;
   out->steps = d.steps;
+  return CGEVAP_OK;
+}
+
+// The device record is laid out as the public one, so it is copied as it is.
+static_assert(sizeof(DevLedger) == sizeof(cgevap_ledger), "ledger layouts");
+static_assert(offsetof(DevLedger, evaporated) == offsetof(cgevap_ledger, evaporated) &&
+                  offsetof(DevLedger, last_removed) == offsetof(cgevap_ledger, last_removed) &&
+                  offsetof(DevLedger, site_steps) == offsetof(cgevap_ledger, site_steps) &&
+                  offsetof(DevLedger, last_sites) == offsetof(cgevap_ledger, last_sites) &&
+                  offsetof(DevLedger, steps) == offsetof(cgevap_ledger, steps),
+              "ledger layouts");
+
+int cgevap_get_ledger_async(cgevap_sim* s, cgevap_ledger* out) {
+  if (!s || !out) return CGEVAP_ERR_ARG;
+  CG_CUDA(s, cudaSetDevice(s->device));
+  CG_CUDA(s, cudaMemcpyAsync(out, s->ledger, sizeof(DevLedger), cudaMemcpyDeviceToHost, s->stream));
   return CGEVAP_OK;
 }
 

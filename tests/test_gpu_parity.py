@@ -213,3 +213,26 @@ def test_recolour_on_pull_restarts_bit_exactly(q, tmp_path):
     pairs = gpu_sim(case, "f32")
     pairs.step(16)
     assert rel_linf(a, pairs.populations(torch.float32).cpu().numpy()) <= 1e-5
+
+
+def test_asynchronous_ledger_reads_match():
+    """cgevap_get_ledger_async: one record per step into its own page-locked slot, enqueued
+    without waiting; after the stream has finished every slot equals what the synchronous read
+    gave for that step, and the last one the oracle's FP64 ledger."""
+    from paper_2412_14859_gb300.binding import Sim
+    case = CASES[0][1]
+    steps = 6
+    run = oracle_run(case, steps)
+    sim = gpu_sim(case, "f64")
+    buf = torch.zeros(40 * steps, dtype=torch.uint8, pin_memory=True)
+    for k in range(steps):
+        sim.step(1)
+        sim.ledger_async(buf[40 * k:40 * (k + 1)])
+    torch.cuda.synchronize()
+    recs = [Sim.ledger_from(buf[40 * k:]) for k in range(steps)]
+    assert [r["steps"] for r in recs] == list(range(1, steps + 1))
+    assert recs[-1] == sim.ledger()
+    assert recs[-1]["evaporated"] == pytest.approx(run.evaporated, rel=1e-12)
+    with pytest.raises(ValueError):
+        sim.ledger_async(torch.zeros(40, dtype=torch.uint8))  # not page-locked
+    sim.close()
