@@ -414,7 +414,8 @@ CGEVAP_API int cgevap_ensemble_autotune(cgevap_ens* ens, int probe_steps, double
  * FP64 ledger fold lives in a static device array of 256 KiB + 256 B, which every GPU that loads
  * the library holds until the process exits; it fits grids of at most 16384 CTAs (for example
  * 192^3 D3Q19 needs 288 for FP32).
- *   p              lattice and physics, validated like cgevap_create (no solids, no flux field);
+ *   p              lattice and physics, validated like cgevap_create (no solids, no flux field;
+ *                  storage CGEVAP_F64, F32, F16DEV or BF16DEV, else ARG);
  *   phi            scalar flux; each site moves phi / S-bar from red to blue rest populations;
  *   dev_state_in   caller-owned state in the handle's internal layout (the raw state bytes of a
  *                  cgevap_save checkpoint).  Populations are stored per direction i on a padded
