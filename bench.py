@@ -453,9 +453,9 @@ def run_adjoint(args, dev):
         "forward_ms": round(fwd, 1), "backward_ms": round(bwd, 1),
         "backward_over_forward": round(bwd / fwd, 2),
         "loss": float(L.detach()), "grad_norm": float(at.grad.norm()),
-        "tape_states": -(-T // K) + K + 3, "forward_bytes_per_update": sb,
+        "tape_states": -(-T // K) + K + 2, "forward_bytes_per_update": sb,
         "launches": "forward: 1 step + 1 volume kernel per step; backward per step: 1 recomputed "
-                    "step + 3 adjoint kernels",
+                    "step + 2 adjoint kernels (A pushes the transposed pull, B1 the stencil)",
         "warmup": "one untimed fit iteration first (first touch of the tape's device memory)",
     }
     sim.close()

@@ -306,7 +306,7 @@ CGEVAP_API long long cgevap_fluid_cells(const cgevap_sim* sim);
  * ledger advance) and record what the backward sweep needs: the state and site bytes at every
  * step that is a multiple of K = min(ckpt_every, T).  Device memory held until
  * cgevap_adjoint_release, cgevap_destroy or a forward run of another (T, K):
- * (ceil(T/K) + K + 3) states of the handle's state size plus (ceil(T/K) + K) site arrays and
+ * (ceil(T/K) + K + 2) states of the handle's state size plus (ceil(T/K) + K) site arrays and
  * 7 per-cell reals; T/K near sqrt(T) minimises it.  dev_volume: caller-owned FP64 [T + 1],
  * receives V(0), ..., V(T) (NULL: not recorded).  Errors: ARG (nsteps < 1 or ckpt_every < 1),
  * UNSUPPORTED (16-bit storage, or the TMA step selected), OOM (tape), CUDA. */

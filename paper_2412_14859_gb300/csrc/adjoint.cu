@@ -6,7 +6,8 @@
 // recomputes the segment's states from its checkpoint into K slots, with the step kernel of the
 // forward run (bitwise the same states and site decisions), then runs the adjoint steps of the
 // segment from its last step down to its first.  Every step is thus computed twice and the
-// device holds ceil(T/K) + K states, plus three adjoint fields of one state each.
+// device holds ceil(T/K) + K states, plus two adjoint fields of one state each (the pushed lg
+// parts of lambda^{n+1} and lambda^n) and one vec2 per cell (their ab part).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -23,10 +24,9 @@ struct AdjointTape {
   uint8_t* ckpt_mask = nullptr;    // nseg site arrays (the mask read by the segment's first step)
   char* seg = nullptr;             // K states: slot k = state after step k of the segment
   uint8_t* seg_mask = nullptr;     // K site arrays: slot k written by step k of the segment
-  char* lam = nullptr;             // 2 states: lambda^{n+1}, lambda^n
-  char* lam_g = nullptr;           // 1 state
+  char* lam = nullptr;             // 2 states: the lg parts of lambda^{n+1} and lambda^n
   void* aux = nullptr;             // kAdjAuxPlanes planes
-  void* ab = nullptr;              // nstore vec2
+  void* ab = nullptr;              // nstore vec2: the ab part of lambda^{n+1} (then of lambda^n)
   DevLedger* led = nullptr;        // ledger of the recomputed steps (discarded)
   // plan of the forward run, checked by the backward sweep
   int family = -1, variant = -1, pc = 0;
@@ -41,8 +41,7 @@ namespace {
 
 void free_tape(AdjointTape* t) {
   if (!t) return;
-  void* ptrs[] = {t->ckpt, t->ckpt_mask, t->seg, t->seg_mask, t->lam, t->lam_g,
-                  t->aux,  t->ab,        t->led};
+  void* ptrs[] = {t->ckpt, t->ckpt_mask, t->seg, t->seg_mask, t->lam, t->aux, t->ab, t->led};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -131,14 +130,14 @@ int make_tape(cgevap_sim* s, int T, int K) {
   const bool ok = dev_alloc(t->ckpt, (size_t)nseg * t->sb) &&
                   dev_alloc(t->ckpt_mask, (size_t)nseg * t->N) &&
                   dev_alloc(t->seg, (size_t)K * t->sb) && dev_alloc(t->seg_mask, (size_t)K * t->N) &&
-                  dev_alloc(t->lam, 2 * t->sb) && dev_alloc(t->lam_g, t->sb) &&
+                  dev_alloc(t->lam, 2 * t->sb) &&
                   dev_alloc(t->aux, kAdjAuxPlanes * ns * real) && dev_alloc(t->ab, 2 * ns * real) &&
                   dev_alloc(t->led, sizeof(DevLedger));
   if (!ok) {
     free_tape(t);
     cudaGetLastError();
     return sim_fail(s, CGEVAP_ERR_OOM, "cannot allocate the adjoint tape (" +
-                                           std::to_string(nseg + K + 3) + " states of " +
+                                           std::to_string(nseg + K + 2) + " states of " +
                                            std::to_string(s->state_bytes) + " bytes)");
   }
   s->tape = t;
@@ -219,7 +218,8 @@ int cgevap_adjoint_backward(cgevap_sim* s, const double* dev_dL_dV, double* dev_
   cudaStream_t st = s->stream;
   const AuxArgs ax = aux_of(s);
   CG_CUDA(s, cudaMemsetAsync(dev_dL_dphi, 0, (size_t)t->N * sizeof(double), st));
-  CG_CUDA(s, cudaMemsetAsync(t->lam, 0, t->sb, st));  // lambda^T = 0
+  CG_CUDA(s, cudaMemsetAsync(t->lam, 0, t->sb, st));  // lambda^T = 0: its lg part ...
+  CG_CUDA(s, cudaMemsetAsync(t->ab, 0, 2 * (size_t)s->geom.nstore * (s->p.storage == CGEVAP_F64 ? 8 : 4), st));  // ... and its ab part
   int lc = 0;                                             // lambda^{n+1} lives in slot lc
   const double inv_sbar = 1.0 / s->p.sbar;
   for (int sg = t->nseg - 1; sg >= 0; --sg) {
@@ -252,14 +252,15 @@ int cgevap_adjoint_backward(cgevap_sim* s, const double* dev_dL_dV, double* dev_
       a.pc = t->apc;
       AdjointOut o;
       o.lam_in = t->lam + (size_t)lc * t->sb;
-      o.lam_g = t->lam_g;
+      o.ab = t->ab;
+      o.lam_g = t->lam + (size_t)(lc ^ 1) * t->sb;
       o.aux = t->aux;
       void* args[] = {&a, &o};
       CG_CUDA(s, cudaLaunchKernel(t->adj.fn, dim3(t->ntx * t->nty, t->anchunk),
                                   dim3(t->adj.threads), args, t->adj.smem, st));
-      CG_CUDA(s, launch_adjoint_stencil(ax, t->aux, t->lam_g, t->ab, mn, dev_dL_dphi, inv_sbar,
+      // B1 reads the ab part of lambda^{n+1} no more (kernel A has): it writes lambda^n's
+      CG_CUDA(s, launch_adjoint_stencil(ax, t->aux, o.lam_g, t->ab, mn, dev_dL_dphi, inv_sbar,
                                         dev_dL_dV ? dev_dL_dV + n + 1 : nullptr, st));
-      CG_CUDA(s, launch_adjoint_gather(ax, t->lam_g, t->ab, t->lam + (size_t)(lc ^ 1) * t->sb, st));
       lc ^= 1;
     }
   }

@@ -16,7 +16,9 @@
 //                lg_total(y) = lg(y) + mu(y) d rho^N/d(rho_r, rho_b) on every direction;
 //                dL/dphi(y) += m(y) (lg_total_0^b(y) - lg_total_0^r(y)) / S-bar     [kernel B1]
 //   (3) pull^T:  lambda^n_j(y) = lg_total_j(y + c_j), or lg_total_{opp j}(y) where y + c_j is
-//                solid or beyond a wall (the transpose of the pull with bounce-back)  [kernel B2]
+//                solid or beyond a wall (the transpose of the pull with bounce-back): kernel A
+//                pushes the lg part to where the pull read from, the next kernel A adds the ab
+//                part of the writer as it reads lambda^{n+1}
 // Kernel A recomputes the forward quantities of its tile exactly as the step does (it runs the
 // step's own tile code with this file's epilogue in place of the collision/store).
 #pragma once
@@ -208,15 +210,36 @@ __device__ __forceinline__ void async_copy(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Kernel A's per-cell tail (replaces StepEpilogue in step_tile): reads lambda^{n+1} at the cell,
-// writes lg (state layout) and the auxiliary planes.  lambda^{n+1} of a cell of plane m is
-// copied into this thread's shared-memory column `lam` (Q vec slots, stride NT) by prefetch(), at
-// the start of the iteration that collides plane m, so the copies overlap the pulls of plane
-// m + 1; cell() waits for them and reads them from shared memory.
+// Kernel A's per-cell tail (replaces StepEpilogue in step_tile).  It reads lambda^{n+1} and
+// writes the transpose of the pull of step n directly:
+//   lambda^n_j(y) = lg_j(y + c_j) + ab(y + c_j), or lg_{opp j}(y) + ab(y) where y + c_j is solid
+// or beyond a wall, with ab = mu d rho^N / d(rho_r, rho_b) from kernel B1 of the same step.  Its
+// lg part is pushed here, each cell x writing lg_i(x) where the pull read g_i(x) from -- slot i
+// of x - c_i, or slot opp(i) of x itself for a bounced link -- so every slot of a fluid cell has
+// exactly one writer.  The ab part is added by the reader: the next adjoint step's kernel A reads
+// the pushed values of its own cell (lam_in) and the ab of the writer, x = y + c_j, from a box
+// of the tile's neighbourhood staged in shared memory per plane.  lambda^{n+1} of a cell of plane
+// m is copied into this thread's shared-memory column `lam` (Q vec slots, stride nt) by prefetch(),
+// at the start of the iteration that collides plane m, so the copies overlap the pulls of plane
+// m + 1; cell() waits for them.  The ab box has four plane slots (m - 1 .. m + 2 in flight): plane
+// um is staged at the start of the iteration that collides um - 1, and its slot was last read by
+// the collision of um - 4, two barriers earlier.
+template <int TX, int TH>
 struct AdjointEpilogue {
   AdjointOut o;
-  unsigned char* lam;  // this thread's column: Q slots of sizeof(vec), stride nt slots
+  unsigned char* lam;   // this thread's column: Q slots of sizeof(vec), stride nt slots
   int nt;
+  unsigned char* abox;  // [4][BY][BX] vec: ab of the planes in flight, one-cell halo
+
+  template <int Q>
+  static constexpr int box_x() { return TX + 2; }
+  template <int Q>
+  static constexpr int box_y() { return Lattice<Q>::D3 ? TH + 2 : 1; }
+  template <int Q, int S>
+  static constexpr int box_bytes() {
+    return 4 * box_x<Q>() * box_y<Q>() * (int)sizeof(typename Storage<S>::vec);
+  }
+
   template <int Q, int S>
   __device__ __forceinline__ void prefetch(const StepArgs& A, int si) const {
     using Vec = typename Storage<S>::vec;
@@ -227,25 +250,64 @@ struct AdjointEpilogue {
     for (int i = 0; i < Q; ++i) async_copy<sizeof(Vec)>(col + (size_t)i * nt, lin + (size_t)i * ns + si);
     async_commit();
   }
+  // ab of plane um (unwrapped) over the tile and its one-cell halo into slot um & 3
+  template <int Q, int S>
+  __device__ __forceinline__ void stage(const StepArgs& A, int a0, int b0, int um, int tid) const {
+    using L = Lattice<Q>;
+    using Vec = typename Storage<S>::vec;
+    constexpr int BX = box_x<Q>(), BY = box_y<Q>(), NB = BX * BY, NT = TX * TH;
+    const Geom& G = A.g;
+    const Plane p = make_plane(G, um);
+    if (!p.ok) return;  // beyond a wall: never read (those links bounce back)
+    const Vec* ab = reinterpret_cast<const Vec*>(o.ab);
+    Vec* box = reinterpret_cast<Vec*>(abox) + (um & 3) * NB;
+    for (int e = tid; e < NB; e += NT) {
+      int a = a0 - 1 + e % BX, b = L::D3 ? b0 - 1 + e / BX : 0;
+      bool ok = true;
+      if (a < 0 || a >= G.na) {
+        if (G.per_a) a = wrap(a, G.na); else ok = false;
+      }
+      if (L::D3 && (b < 0 || b >= G.nb)) {
+        if (G.per_b) b = wrap(b, G.nb); else ok = false;
+      }
+      if (ok) box[e] = __ldg(ab + sidx(G, a, b, p.m));
+    }
+  }
   template <int Q, int S, class R>
-  __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, int si, int /*nimg*/,
+  __device__ __forceinline__ void cell(const StepArgs& A, int /*cell*/, const Slot& sl,
+                                       uint32_t sbits, int m, int si, int /*nimg*/,
                                        const int (&)[3], const R (&g)[Q], R rr, R rb, R irho,
                                        R /*e*/, uint32_t /*flags*/, const R (&rnb)[Q],
                                        int&, R&) const {
+    using L = Lattice<Q>;
     using Vec = typename Storage<S>::vec;
+    constexpr int BX = box_x<Q>(), NB = BX * box_y<Q>();
     const int ns = A.g.nstore;
     Vec* lout = reinterpret_cast<Vec*>(o.lam_g);
+    const PlaneOffsets po = plane_offsets(A.g, m);
+    // this cell's place in the ab box (the tile's own cells need no wrap)
+    const int tile = blockIdx.x;
+    const int bx = sl.a - (tile % A.ntx) * TX + 1;
+    const int by = L::D3 ? sl.b - (tile / A.ntx) * TH + 1 : 0;
+    const Vec* box = reinterpret_cast<const Vec*>(abox);
     async_wait_all();  // this thread's copies of plane m (only it reads its column)
     const Vec* col = reinterpret_cast<const Vec*>(lam);
     auto lam_at = [&](int i) -> V2<R> {
       const Vec v = col[(size_t)i * nt];
-      return {v.x, v.y};
+      // ab of the slot's writer: x = y + c_i, or y itself where y + c_i is solid (the source of
+      // this cell's direction opp(i))
+      const bool self = i == 0 || ((sbits >> opp(i)) & 1u);
+      const Vec w = self ? box[(m & 3) * NB + by * BX + bx]
+                         : box[((m + L::cm(i)) & 3) * NB + (by + L::cb(i)) * BX + bx + L::ca(i)];
+      return {v.x + w.x, v.y + w.y};
     };
     auto lg_out = [&](int i, V2<R> v2) {
       Vec v;
       v.x = v2.r;
       v.y = v2.b;
-      lout[(size_t)i * ns + si] = v;
+      const bool bounce = (sbits >> i) & 1u;
+      const int dst = bounce ? si : pull_source<L>(sl, po, si, i);
+      lout[(size_t)(bounce ? opp(i) : i) * ns + dst] = v;
     };
     R lF[3];
     collide_adjoint<Q, R>(A.ph, g, rr, rb, irho, rnb, lam_at, lg_out, lF);
@@ -266,11 +328,13 @@ __global__ void __launch_bounds__(TX* TY, (S == ST_F64 ? 256 : 384) / (TX * TY))
   long long n = 0;
   double d = 0.0;
   using Vec = typename Storage<S>::vec;
-  // lambda columns after the tile's own shared memory: slot i of thread t at (i TX TY + t)
-  const AdjointEpilogue E{O, dyn_smem + TileSmem<Q, S, TX, TY, 1>::BYTES + threadIdx.x * sizeof(Vec),
-                          TX * TY};
-  step_tile<Q, S, TX, TY, 1, AdjointEpilogue>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d,
-                                              threadIdx.x, -1, E);
+  using Epi = AdjointEpilogue<TX, TY>;
+  // lambda columns after the tile's own shared memory (slot i of thread t at i TX TY + t), then
+  // the ab box
+  constexpr int lam_bytes = Q * TX * TY * (int)sizeof(Vec);
+  unsigned char* const lam0 = dyn_smem + TileSmem<Q, S, TX, TY, 1>::BYTES;
+  const Epi E{O, lam0 + threadIdx.x * sizeof(Vec), TX * TY, lam0 + lam_bytes};
+  step_tile<Q, S, TX, TY, 1, Epi>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d, threadIdx.x, -1, E);
 }
 
 __device__ __forceinline__ void cell_coords(const Geom& g, int cell, int& a, int& b, int& m) {
@@ -322,43 +386,6 @@ __global__ void __launch_bounds__(256)
   if (mask[cell] & 1u) {  // Eq. (exchange): d g_0^r / d phi = -1/S-bar, d g_0^b / d phi = +1/S-bar
     const Vec l0 = reinterpret_cast<const Vec*>(lam_g)[si];
     dphi[cell] += ((double)(l0.y + v.y) - (double)(l0.x + v.x)) * inv_sbar;
-  }
-}
-
-// (3) one thread per cell: the pull transposed.
-template <int Q, class R>
-__global__ void __launch_bounds__(256)
-    cg_adjoint_gather_kernel(Geom G, const void* __restrict__ lam_g, const void* __restrict__ ab,
-                             void* __restrict__ lam_out) {
-  using L = Lattice<Q>;
-  using Vec = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= G.ncell) return;
-  int a, b, m;
-  cell_coords(G, cell, a, b, m);
-  const Slot sl = make_slot<L>(G, a, b);
-  const Plane p = make_plane(G, m);
-  uint32_t bits = 0;
-  if (!solid_bits<L>(G, sl, p, cell, bits)) return;
-  const PlaneOffsets po = plane_offsets(G, m);
-  const int si = sidx(G, a, b, m);
-  const size_t ns = G.nstore;
-  const Vec* lg = reinterpret_cast<const Vec*>(lam_g);
-  const Vec* abv = reinterpret_cast<const Vec*>(ab);
-  Vec* out = reinterpret_cast<Vec*>(lam_out);
-#pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    int src = si, dir = j;
-    if (j != 0) {
-      if ((bits >> opp(j)) & 1u) dir = opp(j);          // y + c_j solid: bounce-back link
-      else src = pull_source<L>(sl, po, si, opp(j));     // y + c_j
-    }
-    const Vec l = __ldg(lg + (size_t)dir * ns + src);
-    const Vec w = __ldg(abv + src);
-    Vec v;
-    v.x = l.x + w.x;
-    v.y = l.y + w.y;
-    out[(size_t)j * ns + si] = v;
   }
 }
 

@@ -9,9 +9,11 @@ namespace {
 
 template <int Q, int S, int TX, int TY>
 KernelRef adj_ref() {
-  // the tile's shared memory, then the prefetched lambda^{n+1} columns (Q vec per thread)
+  // the tile's shared memory, then the prefetched lambda^{n+1} columns (Q vec per thread), then
+  // the box of ab
   constexpr int smem = TileSmem<Q, S, TX, TY, 1>::BYTES +
-                       Q * TX * TY * (int)sizeof(typename Storage<S>::vec);
+                       Q * TX * TY * (int)sizeof(typename Storage<S>::vec) +
+                       AdjointEpilogue<TX, TY>::template box_bytes<Q, S>();
   const void* fn = (const void*)cg_adjoint_local_kernel<Q, S, TX, TY>;
   static bool attr = false;
   if (!attr) {
@@ -57,23 +59,6 @@ cudaError_t launch_adjoint_stencil(const AuxArgs& a, const void* aux, const void
   else if (a.q == 9 && a.storage == ST_F32)
     cg_adjoint_stencil_kernel<9, float><<<nb, kThreads, 0, s>>>(
         a.g, (const float*)aux, lam_g, ab, mask, dphi, inv_sbar, dLdV);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_gather(const AuxArgs& a, const void* lam_g, const void* ab,
-                                  void* lam_out, cudaStream_t s) {
-  if (a.g.ncell <= 0) return cudaSuccess;
-  const unsigned nb = blocks_for(a.g.ncell);
-  if (a.q == 19 && a.storage == ST_F64)
-    cg_adjoint_gather_kernel<19, double><<<nb, kThreads, 0, s>>>(a.g, lam_g, ab, lam_out);
-  else if (a.q == 19 && a.storage == ST_F32)
-    cg_adjoint_gather_kernel<19, float><<<nb, kThreads, 0, s>>>(a.g, lam_g, ab, lam_out);
-  else if (a.q == 9 && a.storage == ST_F64)
-    cg_adjoint_gather_kernel<9, double><<<nb, kThreads, 0, s>>>(a.g, lam_g, ab, lam_out);
-  else if (a.q == 9 && a.storage == ST_F32)
-    cg_adjoint_gather_kernel<9, float><<<nb, kThreads, 0, s>>>(a.g, lam_g, ab, lam_out);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

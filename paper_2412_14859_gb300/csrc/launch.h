@@ -93,19 +93,19 @@ cudaError_t launch_heated_flux(const AuxArgs& a, const void* state, double* part
 // dL/dF_a, dL/dF_b, dL/dF_m, d rho^N/d rho_r, d rho^N/d rho_b.
 constexpr int kAdjAuxPlanes = 5;
 struct AdjointOut {
-  const void* lam_in;  // lambda^{n+1} = dL/df^{n+1}, state layout (vec2 per direction, index)
-  void* lam_g;         // out: dL/dg through each cell's own collision, state layout
+  const void* lam_in;  // the lg part of lambda^{n+1} = dL/df^{n+1}, pushed by the previous
+                       // adjoint step (state layout: vec2 per direction and storage index)
+  const void* ab;      // the ab part of lambda^{n+1}: nstore vec2 from kernel B1 of that step
+  void* lam_g;         // out: the lg part of lambda^n, pushed to where the pull of step n read
   void* aux;           // out: kAdjAuxPlanes planes
 };
 KernelRef adjoint_local_kernel(int q, int storage);
 // Kernel B1: stencil transpose, exchange derivative into dphi (FP64, compact [N]); aux holds
-// kAdjAuxPlanes planes of nstore reals; ab receives nstore vec2.  dLdV may be nullptr.
+// kAdjAuxPlanes planes of nstore reals; lam_g is kernel A's pushed output (its rest slot of a
+// cell is that cell's own lg_0); ab receives nstore vec2.  dLdV may be nullptr.
 cudaError_t launch_adjoint_stencil(const AuxArgs& a, const void* aux, const void* lam_g, void* ab,
                                    const uint8_t* mask, double* dphi, double inv_sbar,
                                    const double* dLdV, cudaStream_t s);
-// Kernel B2: the pull transposed, lam_out = lambda^n in the state layout.
-cudaError_t launch_adjoint_gather(const AuxArgs& a, const void* lam_g, const void* ab,
-                                  void* lam_out, cudaStream_t s);
 // Liquid volume of a state into *out (FP64); part holds kVolumeBlocks doubles, *done starts at 0.
 constexpr int kVolumeBlocks = 152 * 16;  // 16 CTAs of 256 threads per SM: loads in flight
 cudaError_t launch_volume(const AuxArgs& a, const void* state, double* part, unsigned int* done,

@@ -847,9 +847,17 @@ struct StepEpilogue {
   // of plane m can start fetching it here (the step itself reads nothing more).
   template <int Q, int S>
   __device__ __forceinline__ void prefetch(const StepArgs&, int /*si*/) const {}
-  // (lr, lb): the rounding errors of rr, rb (16-bit storages: rr + lr is the exact mass)
+  // Called by every thread of the tile (origin a0, b0), for plane um, before the barrier that
+  // precedes the collision of plane um - 1 (and for the chunk's planes m0 - 1 and m0 before the
+  // first one): an epilogue that reads per-cell data of the neighbours stages it here.
+  template <int Q, int S>
+  __device__ __forceinline__ void stage(const StepArgs&, int /*a0*/, int /*b0*/, int /*um*/,
+                                        int /*tid*/) const {}
+  // sl, sbits, m: the cell's slot, solid-link bits and plane.  (lr, lb): the rounding errors of
+  // rr, rb (16-bit storages: rr + lr is the exact mass)
   template <int Q, int S, class R>
-  __device__ __forceinline__ void cell(const StepArgs& A, int cell, int si, int nimg,
+  __device__ __forceinline__ void cell(const StepArgs& A, int cell, const Slot& /*sl*/,
+                                       uint32_t /*sbits*/, int /*m*/, int si, int nimg,
                                        const int (&dimg)[3], const R (&f)[Q], R rr, R rb,
                                        R irho, R e, uint32_t flags, const R (&rnb)[Q],
                                        int& n_sites, R& removed, R lr = R(0), R lb = R(0)) const {
@@ -1241,6 +1249,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       stage_rest(um + 2);
   };
 
+  epi.template stage<Q, S>(A, a0, b0, m0 - 1, tid);
+  epi.template stage<Q, S>(A, a0, b0, m0, tid);
   issue(m0 - 1);  // PF: the first fill's own pulls
   stage_rest(m0 - 2);
   stage_rest(m0 - 1);
@@ -1269,6 +1279,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       __syncthreads();
       continue;
     }
+    epi.template stage<Q, S>(A, a0, b0, m + 1, tid);
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
       if (active[c] && cur[c].ok) epi.template prefetch<Q, S>(A, sidx(G, me[c].a, me[c].b, m));
@@ -1304,13 +1315,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int tile, int chunk
       }
       const int cell = (m * G.nb + me[c].b) * G.na + me[c].a;
       if constexpr (DEV || RC16IN || EXACTP)
-        epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
-                                cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
-                                nloc, rem, cur[c].lr, cur[c].lb);
+        epi.template cell<Q, S>(A, cell, me[c], cur[c].bits, m, sidx(G, me[c].a, me[c].b, m),
+                                nimg[c], dimg[c], own, cur[c].rr, cur[c].rb, cur[c].irho,
+                                cur[c].e, cur[c].flags, rnb, nloc, rem, cur[c].lr, cur[c].lb);
       else
-        epi.template cell<Q, S>(A, cell, sidx(G, me[c].a, me[c].b, m), nimg[c], dimg[c], own,
-                                cur[c].rr, cur[c].rb, cur[c].irho, cur[c].e, cur[c].flags, rnb,
-                                nloc, rem);
+        epi.template cell<Q, S>(A, cell, me[c], cur[c].bits, m, sidx(G, me[c].a, me[c].b, m),
+                                nimg[c], dimg[c], own, cur[c].rr, cur[c].rb, cur[c].irho,
+                                cur[c].e, cur[c].flags, rnb, nloc, rem);
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) cur[c] = nxt[c];
