@@ -285,10 +285,10 @@ struct AdjointEpilogue {
     const int ns = A.g.nstore;
     Vec* lout = reinterpret_cast<Vec*>(o.lam_g);
     const PlaneOffsets po = plane_offsets(A.g, m);
-    // this cell's place in the ab box (the tile's own cells need no wrap)
-    const int tile = blockIdx.x;
-    const int bx = sl.a - (tile % A.ntx) * TX + 1;
-    const int by = L::D3 ? sl.b - (tile / A.ntx) * TH + 1 : 0;
+    // this cell's place in the ab box: the thread's own column of the tile (one cell per thread
+    // and plane), one in from the halo
+    const int bx = (int)threadIdx.x % TX + 1;
+    const int by = L::D3 ? (int)threadIdx.x / TX + 1 : 0;
     const Vec* box = reinterpret_cast<const Vec*>(abox);
     async_wait_all();  // this thread's copies of plane m (only it reads its column)
     const Vec* col = reinterpret_cast<const Vec*>(lam);
