@@ -636,7 +636,7 @@ def run_ours(args, d: Dist):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     storages = [s for s in args.storages.split(",") if s]
-    results, rho_r = {}, {}
+    results, rho_r, rho_b = {}, {}, {}
 
     for st in storages:
         K = args.steps
@@ -671,6 +671,7 @@ def run_ours(args, d: Dist):
             # the state after warm-up + K steps, compared across storages below
             m = sim.macros()
             rho_r[st] = m["rho_r"]
+            rho_b[st] = m["rho_b"]
             led = sim.ledger()
             mass_r = float(m["rho_r"].sum())
             # headline storage: more replays of the same graph, each timed on its own, so that
@@ -707,6 +708,7 @@ def run_ours(args, d: Dist):
                 "steps": r["steps_total"],
                 "rel_mass_error_red": abs(r["mass_r"] - results[ref]["mass_r"]) / results[ref]["mass_r"],
                 "rel_linf_rho_r": float((a - b).abs().max() / b.abs().max()),
+                "rel_linf_rho_b": float((rho_b[st] - rho_b[ref]).abs().max() / rho_b[ref].abs().max()),
                 "rel_error_evaporated_ledger": abs(r["ledger"] - results[ref]["ledger"]) / max(results[ref]["ledger"], 1e-300),
             }
         variants[st] = v
