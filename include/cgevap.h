@@ -49,7 +49,7 @@ extern "C" {
 #define CGEVAP_ERR_OOM -3          /* device or host allocation failed                        */
 #define CGEVAP_ERR_TIMEOUT -4      /* a bounded device-side wait gave up                      */
 #define CGEVAP_ERR_NAN -5          /* the health check found a non-finite or negative density */
-#define CGEVAP_ERR_UNSUPPORTED -6  /* valid request this build does not provide               */
+#define CGEVAP_ERR_UNSUPPORTED -6  /* valid request the library does not support               */
 #define CGEVAP_ERR_IO -7           /* checkpoint file could not be read or written            */
 
 /* ---- evaporation-site rules ---- */
