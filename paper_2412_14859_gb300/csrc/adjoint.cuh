@@ -219,7 +219,7 @@ __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_a
 // exactly one writer.  The ab part is added by the reader: the next adjoint step's kernel A reads
 // the pushed values of its own cell (lam_in) and the ab of the writer, x = y + c_j, from a box
 // of the tile's neighbourhood staged in shared memory per plane.  lambda^{n+1} of a cell of plane
-// m is copied into this thread's shared-memory column `lam` (Q vec slots, stride nt) by prefetch(),
+// m is copied into this thread's shared-memory column `lam` (Q vec slots, stride TX TH) by prefetch(),
 // at the start of the iteration that collides plane m, so the copies overlap the pulls of plane
 // m + 1; cell() waits for them.  The ab box has four plane slots (m - 1 .. m + 2 in flight): plane
 // um is staged at the start of the iteration that collides um - 1, and its slot was last read by
@@ -227,8 +227,7 @@ __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_a
 template <int TX, int TH>
 struct AdjointEpilogue {
   AdjointOut o;
-  unsigned char* lam;   // this thread's column: Q slots of sizeof(vec), stride nt slots
-  int nt;
+  unsigned char* lam;   // this thread's column: Q slots of sizeof(vec), stride TX TH slots
   unsigned char* abox;  // [4][BY][BX] vec: ab of the planes in flight, one-cell halo
 
   template <int Q>
@@ -247,7 +246,7 @@ struct AdjointEpilogue {
     const Vec* lin = reinterpret_cast<const Vec*>(o.lam_in);
     Vec* col = reinterpret_cast<Vec*>(lam);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) async_copy<sizeof(Vec)>(col + (size_t)i * nt, lin + (size_t)i * ns + si);
+    for (int i = 0; i < Q; ++i) async_copy<sizeof(Vec)>(col + i * (TX * TH), lin + (size_t)i * ns + si);
     async_commit();
   }
   // ab of plane um (unwrapped) over the tile and its one-cell halo into slot um & 3
@@ -293,7 +292,7 @@ struct AdjointEpilogue {
     async_wait_all();  // this thread's copies of plane m (only it reads its column)
     const Vec* col = reinterpret_cast<const Vec*>(lam);
     auto lam_at = [&](int i) -> V2<R> {
-      const Vec v = col[(size_t)i * nt];
+      const Vec v = col[i * (TX * TH)];
       // ab of the slot's writer: x = y + c_i, or y itself where y + c_i is solid (the source of
       // this cell's direction opp(i))
       const bool self = i == 0 || ((sbits >> opp(i)) & 1u);
@@ -305,9 +304,10 @@ struct AdjointEpilogue {
       Vec v;
       v.x = v2.r;
       v.y = v2.b;
+      // element index in 32 bits (a state holds Q nstore < 2^31 vec2)
       const bool bounce = (sbits >> i) & 1u;
-      const int dst = bounce ? si : pull_source<L>(sl, po, si, i);
-      lout[(size_t)(bounce ? opp(i) : i) * ns + dst] = v;
+      const int idx = bounce ? opp(i) * ns + si : i * ns + pull_source<L>(sl, po, si, i);
+      lout[idx] = v;
     };
     R lF[3];
     collide_adjoint<Q, R>(A.ph, g, rr, rb, irho, rnb, lam_at, lg_out, lF);
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(TX* TY, (S == ST_F64 ? 256 : 384) / (TX * TY))
   // the ab box
   constexpr int lam_bytes = Q * TX * TY * (int)sizeof(Vec);
   unsigned char* const lam0 = dyn_smem + TileSmem<Q, S, TX, TY, 1>::BYTES;
-  const Epi E{O, lam0 + threadIdx.x * sizeof(Vec), TX * TY, lam0 + lam_bytes};
+  const Epi E{O, lam0 + threadIdx.x * sizeof(Vec), lam0 + lam_bytes};
   step_tile<Q, S, TX, TY, 1, Epi>(A, blockIdx.x, blockIdx.y, dyn_smem, n, d, threadIdx.x, -1, E);
 }
 
