@@ -141,17 +141,18 @@ template <int S, int Q>
 struct PopIO<S, Q, false> {
   using R = typename Storage<S>::real;
   using Vec = typename Storage<S>::vec;
-  // Population of direction `dir` stored at storage index `si`, delivered as direction i.
+  // Population of direction `dir` stored at storage index `si`, delivered as direction i.  The
+  // element index is formed in 32 bits: a state holds Q nstore < 2^31 pairs (checked at create).
   static __device__ __forceinline__ V2<R> load(const void* base, int nstore, int /*i*/, int dir,
                                                int si, const Physics&) {
-    const Vec* p = reinterpret_cast<const Vec*>(base) + (size_t)dir * nstore + si;
+    const Vec* p = reinterpret_cast<const Vec*>(base) + (dir * nstore + si);
     Vec v = __ldg(p);
     return {v.x, v.y};
   }
   // Stores one population pair at storage index si; f0 is the rest pair (unused here).
   static __device__ __forceinline__ void store(void* base, int nstore, int i, int si, R r, R b,
                                                V2<R>, const Physics&) {
-    Vec* p = reinterpret_cast<Vec*>(base) + (size_t)i * nstore + si;
+    Vec* p = reinterpret_cast<Vec*>(base) + (i * nstore + si);
     Vec v;
     v.x = r;
     v.y = b;
