@@ -74,3 +74,16 @@ def test_null_handles_rejected(lib):
     assert lib.cgevap_get_flux_field(None, None) == -1
     assert lib.cgevap_destroy(None) == 0
     assert lib.cgevap_bytes_per_update(None) == 0.0
+    assert lib.cgevap_get_ledger_async(None, None) == -1
+
+
+def test_ledger_record_decodes():
+    """The 40-byte record cgevap_get_ledger_async copies is the public cgevap_ledger; the
+    binding decodes it from a byte tensor."""
+    import torch
+    from paper_2412_14859_gb300.binding import Ledger, Sim
+    assert ctypes.sizeof(Ledger) == 40
+    rec = Ledger(evaporated=1.5, last_removed=0.25, site_steps=7, last_sites=3, steps=9)
+    buf = torch.frombuffer(bytearray(bytes(rec) + bytes(8)), dtype=torch.uint8)
+    assert Sim.ledger_from(buf) == {"evaporated": 1.5, "last_removed": 0.25, "site_steps": 7,
+                                    "last_sites": 3, "steps": 9}
